@@ -1,0 +1,347 @@
+"""QLC codec benchmark on GB300 (one JSON line on stdout).
+
+Workload: one 256 MiB e4m3 tensor shaped [16384 x 16384] (block-32 absmax
+scaled Student-t(4) values, seed = rank), chunk 4096 symbols, Table 1 scheme.
+A step is one pass of the whole hot path over it: histogram -> LUT ->
+encode -> decode (every kernel of libqlc), followed by nothing on the host.
+value = raw bytes per second over all ranks (replicas, no collective).
+
+Legs: the device-timed step (CUDA events on the launching stream, inputs
+resident in HBM), per-kernel durations from events between the launches, an
+end-to-end leg through the same C ABI with pinned host buffers (host->device
+copy of the input, encode, container read back, container copied in,
+decode, decoded bytes read back), and the CPU oracle on a bounded sample of
+the same tensor.  --impl reference times the CPU oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BYTES = 16384 * 16384
+CHUNK = 4096
+SCHEME = 1
+WORKLOAD = "qlc_roundtrip_256MiB_t4_e4m3"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_for(kernel_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current source of the kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_2602_17849_gb300", "csrc", kernel_file)
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            f = line.split()
+            if len(f) >= 4 and f[0] == kernel_file and f[1] == digest and f[2] == WORKLOAD:
+                return float(f[3])
+    except OSError:
+        pass
+    return None
+
+
+def cpu_oracle_roundtrip(x_host, budget_s: float = 10.0, slice_bytes: int = 16 << 20):
+    """Oracle histogram + rank + encode + decode on consecutive slices of x_host
+    until about budget_s of CPU time; returns (bytes, seconds, slices)."""
+    import numpy as np
+
+    import oracle
+    done, t = 0, 0.0
+    n = x_host.size
+    while done < n and t < budget_s:
+        s = x_host[done:done + slice_bytes]
+        t0 = time.perf_counter()
+        c = oracle.encode(s, scheme_id=SCHEME, chunk_symbols=CHUNK)
+        st, y, _ = oracle.decode(c)
+        t += time.perf_counter() - t0
+        assert st == 0 and np.array_equal(y, s)
+        done += s.size
+    return done, t
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle on the host cores (rank 0 only)."""
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    import torch
+
+    from paper_2602_17849_gb300 import inputs
+    x = inputs.make_e4m3("t4", N_BYTES, seed=0).numpy()
+    slice_bytes = 16 << 20
+    for _ in range(args.warmup):
+        cpu_oracle_roundtrip(x[:slice_bytes], budget_s=1e9, slice_bytes=slice_bytes)
+    times = []
+    for k in range(args.steps):
+        off = (k * slice_bytes) % N_BYTES
+        b, t = cpu_oracle_roundtrip(x[off:off + slice_bytes], budget_s=1e9, slice_bytes=slice_bytes)
+        times.append(t)
+    tot = sum(times)
+    value = args.steps * slice_bytes / tot / 1e9
+    sample = f"{slice_bytes >> 20} MiB slice of the 256 MiB tensor per step (oracle encode+decode)"
+    line = {
+        "metric": "QLC encode+decode round trip, raw GB/s", "value": value, "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "n_bytes": N_BYTES, "chunk_symbols": CHUNK, "scheme": SCHEME},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    del torch
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2602_17849_gb300 import _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2602_17849_gb300 import inputs, qlc
+
+    x = inputs.make_e4m3("t4", N_BYTES, seed=rank, device=dev)
+    codec = qlc.Codec(N_BYTES, CHUNK, SCHEME, dev)
+    cont = codec.new_container()
+    y = torch.empty(N_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        qlc.qlc_histogram(x, codec.hist, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        qlc.qlc_build_lut(codec.hist, SCHEME, codec.lut, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        qlc.qlc_encode(x, codec.lut, CHUNK, cont, codec.ws, codec.out_bytes, codec.status, stream=stream)
+        if ev:
+            ev[3].record(stream)
+        qlc.qlc_decode(cont, y, codec.n_out, codec.status, stream=stream)
+        if ev:
+            ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    codec.check()
+    c_bytes = int(codec.out_bytes.item())
+    assert torch.equal(x, y), "round trip is not bit-exact"
+
+    # per-kernel durations (events between launches, same stream)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        start.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        end.record(stream)
+        torch.cuda.synchronize()
+        time.sleep(0.1)
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(end) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    codec.check()
+    assert torch.equal(x, y), "round trip is not bit-exact"
+
+    seg = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs])  # ms
+    hist_ms, lut_ms, enc_ms, dec_ms = seg.mean(axis=0)
+
+    # ---- e2e through the C ABI with pinned host buffers
+    hx = torch.empty(N_BYTES, dtype=torch.uint8, pin_memory=True)
+    hx.copy_(x)
+    hc = torch.empty(codec.cap, dtype=torch.uint8, pin_memory=True)
+    hy = torch.empty(N_BYTES, dtype=torch.uint8, pin_memory=True)
+    hb = torch.empty(1, dtype=torch.int64, pin_memory=True)
+    xin = torch.empty_like(x)
+    cin = torch.empty_like(cont)
+
+    def e2e_step():
+        xin.copy_(hx, non_blocking=True)
+        qlc.qlc_histogram(xin, codec.hist, stream=stream)
+        qlc.qlc_build_lut(codec.hist, SCHEME, codec.lut, stream=stream)
+        qlc.qlc_encode(xin, codec.lut, CHUNK, cont, codec.ws, codec.out_bytes, codec.status, stream=stream)
+        hb.copy_(codec.out_bytes, non_blocking=True)
+        stream.synchronize()
+        nb = int(hb.item())
+        hc[:nb].copy_(cont[:nb], non_blocking=True)
+        cin[:nb].copy_(hc[:nb], non_blocking=True)
+        qlc.qlc_decode(cin, y, codec.n_out, codec.status, in_bytes=nb, stream=stream)
+        hy.copy_(y, non_blocking=True)
+        stream.synchronize()
+        return nb
+
+    for _ in range(2):
+        e2e_step()
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        nb = e2e_step()
+        e2e_t.append(time.perf_counter() - t0)
+    assert torch.equal(hy, hx)
+    e2e_s = statistics.median(e2e_t)
+
+    # ---- roofline of the dominant kernel
+    peak, peak_kind = _peaks()
+    r = c_bytes / N_BYTES
+    kern = {"hist": (hist_ms, N_BYTES, "hist_lut.cu"), "lut": (lut_ms, 256 * 8 + 800, "hist_lut.cu"),
+            "encode": (enc_ms, N_BYTES + c_bytes, "encode.cu"),
+            "decode": (dec_ms, N_BYTES + c_bytes, "decode.cu")}
+    dom = max(kern, key=lambda k: kern[k][0])
+    d_ms, d_bytes, d_file = kern[dom]
+    achieved = d_bytes / (d_ms * 1e-3) / 1e9
+    traffic = _traffic_for(d_file)
+
+    # compressibility (a6): code-only from the histogram, container from its size
+    h = codec.hist.cpu().numpy().astype(np.int64)
+    lut = codec.lut.cpu().numpy()
+    lens = (lut[32:544].view(np.uint16) & 15).astype(np.int64)
+    code_bits = int((h * lens).sum())
+
+    line = {
+        "metric": "QLC encode+decode round trip, raw GB/s", "value": world * N_BYTES / (ms_max * 1e-3) / 1e9,
+        "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "shape": [16384, 16384], "n_bytes": N_BYTES,
+                   "chunk_symbols": CHUNK, "scheme": "Table 1", "kind": "student_t4_block32_e4m3",
+                   "l2": "inputs larger than L2 (256 MiB in, ~230 MB container, 256 MiB out per step)",
+                   "parallelism": f"replicas x{world}"},
+        "kernels_ms": {"histogram": hist_ms, "build_lut": lut_ms, "encode": enc_ms, "decode": dec_ms},
+        "encode_gbs": N_BYTES / ((hist_ms + lut_ms + enc_ms) * 1e-3) / 1e9,
+        "encode_lut_given_gbs": N_BYTES / (enc_ms * 1e-3) / 1e9,
+        "decode_gbs": N_BYTES / (dec_ms * 1e-3) / 1e9,
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes": d_bytes},
+        "roofline_all": {k: {"achieved": v[1] / (v[0] * 1e-3) / 1e9, "frac": v[1] / (v[0] * 1e-3) / 1e9 / peak}
+                         for k, v in kern.items() if k != "lut"},
+        "compressibility": {"container": 1 - r, "code_only": 1 - code_bits / (8 * N_BYTES),
+                            "container_bytes": c_bytes},
+        "e2e": {"value": N_BYTES / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": N_BYTES + nb,
+                "d2h_bytes_per_step": 8 + nb + N_BYTES},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1:
+        xh = x.cpu().numpy()
+        b, s = cpu_oracle_roundtrip(xh, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": b / s / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                "sample": f"first {b >> 20} MiB of the tensor in 16 MiB slices, "
+                                          f"oracle encode+decode, {s:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,372 @@
+// encode.cu -- QLC encoder (Sections 5 and 7) writing container v1.
+//
+// One persistent kernel.  CTAs take groups (32 chunks) in ticket order:
+//   pass 1  each warp sums the code lengths of its chunks -> chunk_bits;
+//   look-back  the group publishes its padded byte size and finds the sum of
+//           all earlier groups' sizes (decoupled look-back, bounded waits);
+//   pass 2  the group's symbols are re-read (from L2: at most two groups per
+//           SM are in flight) and packed, 4096 symbols per tile: block scan of
+//           per-thread bit counts, MSB-first packing of each thread's 16
+//           codewords into a shared staging window, coalesced 16-byte stores
+//           of every completed 16-byte block.
+// HBM traffic is one read of the input and one write of the container.
+#include "qlc_common.cuh"
+
+namespace qlc {
+
+constexpr int kEncThreads = 256;
+constexpr int kEncWarps = kEncThreads / 32;
+constexpr int kTile = kEncThreads * 16;
+constexpr int kStageWords = 4 + (kTile * kMaxCode + 31) / 32 + 4;
+constexpr int kPass1Unroll = 8;
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kFlagError = 3ull << 62;
+constexpr unsigned long long kValMask = (1ull << 62) - 1;
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per look-back wait
+
+__device__ __forceinline__ uint32_t fold(uint32_t b) { return b + (b >> 7); }
+
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t len16(const uint32_t* s_len, uint4 q) {
+  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) s += s_len[fold((w[k] >> (8 * j)) & 0xFFu)];
+  return s;
+}
+
+// Decoupled look-back over groups (warp-wide).  Publishes this group's size,
+// returns the byte offset of the group (sum of all earlier groups' sizes).
+// Every wait is bounded; on timeout *err is set and an error flag is
+// published so that later groups stop waiting too.
+__device__ unsigned long long lookback(unsigned long long* gstat, uint64_t g, uint64_t gbytes,
+                                       int lane, bool* err) {
+  *err = false;
+  if (g == 0) {
+    if (lane == 0) st_release_u64(&gstat[0], kFlagPrefix | gbytes);
+    return 0;
+  }
+  if (lane == 0) st_release_u64(&gstat[g], kFlagAgg | gbytes);
+  unsigned long long excl = 0;
+  int64_t idx = (int64_t)g - 1 - lane;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    unsigned long long v = kFlagPrefix;  // lanes before group 0 (never reached)
+    if (idx >= 0) {
+      while (true) {
+        v = ld_acquire_u64(&gstat[idx]);
+        if (v >> 62) break;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+          v = kFlagError;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    const unsigned flag = (unsigned)(v >> 62);
+    const unsigned stop = __ballot_sync(0xffffffffu, flag >= 2);
+    if (stop) {
+      const int k = __ffs(stop) - 1;  // nearest earlier group with a full prefix
+      const unsigned bad = __ballot_sync(0xffffffffu, flag == 3 && lane <= k);
+      excl += warp_sum_u64(lane <= k ? (v & kValMask) : 0ull);
+      *err = bad != 0;
+      break;
+    }
+    excl += warp_sum_u64(v & kValMask);
+    idx -= 32;
+  }
+  if (lane == 0) st_release_u64(&gstat[g], (*err ? kFlagError : kFlagPrefix) | (excl + gbytes));
+  return excl;
+}
+
+__device__ void write_header(uint8_t* out, uint64_t n, uint32_t cs, uint64_t n_chunks,
+                             const qlc_lut* lut, int tid) {
+  if (tid == 0) {
+    *reinterpret_cast<uint32_t*>(out + 0) = 0x31434C51u;  // "QLC1"
+    *reinterpret_cast<uint16_t*>(out + 4) = QLC_VERSION;
+    out[6] = lut->scheme.id;
+    out[7] = 0;
+    *reinterpret_cast<unsigned long long*>(out + 8) = n;
+    *reinterpret_cast<uint32_t*>(out + 16) = cs;
+    *reinterpret_cast<uint32_t*>(out + 20) = (uint32_t)n_chunks;
+    *reinterpret_cast<unsigned long long*>(out + 56) = 0;
+  }
+  if (tid < 8) {
+    *reinterpret_cast<uint16_t*>(out + 24 + 2 * tid) = lut->scheme.area_n[tid];
+    out[40 + tid] = lut->scheme.area_bits[tid];
+  }
+  if (tid < 256) out[64 + tid] = lut->dec[tid];
+  const uint64_t idx_end = kIndexOff + 8 * n_groups_of(n_chunks) + 2 * n_chunks;
+  const uint64_t P = payload_start(n_chunks);
+  if (idx_end + tid < P) out[idx_end + tid] = 0;
+}
+
+__global__ void __launch_bounds__(kEncThreads, 2)
+encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restrict__ lut,
+              uint32_t cs, uint8_t* __restrict__ out, unsigned int* __restrict__ ticket,
+              unsigned long long* __restrict__ gstat, unsigned long long* __restrict__ out_bytes,
+              uint32_t* __restrict__ status) {
+  __shared__ uint32_t s_enc[257];  // MSB-aligned codeword | length, index fold(symbol)
+  __shared__ uint32_t s_len[257];
+  __shared__ uint32_t s_stage[kStageWords];
+  __shared__ uint32_t s_chunk_bits[kGroupChunks];
+  __shared__ uint32_t s_warp[kEncWarps];
+  __shared__ unsigned long long s_group;
+  __shared__ unsigned long long s_excl;
+  __shared__ int s_err;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    // A LUT entry must be a codeword of 3..11 bits; anything else (a LUT not
+    // made by qlc_build_lut*) would overrun the staging window and the
+    // output bound, so the kernel refuses it.
+    const uint32_t e = lut->enc[tid];
+    const uint32_t len = e & 15u, code = e >> 4;
+    const bool bad = len < 3 || len > kMaxCode || (code >> len) != 0;
+    if (__syncthreads_or(bad)) {
+      if (blockIdx.x == 0 && tid == 0) set_status(status, QLC_ERR_ARG);
+      return;
+    }
+    s_enc[fold(tid)] = (code << (32 - len)) | len;
+    s_len[fold(tid)] = len;
+  }
+  for (int i = tid; i < kStageWords; i += kEncThreads) s_stage[i] = 0;
+
+  const uint64_t n_chunks = (n + cs - 1) / cs;
+  const uint64_t n_groups = n_groups_of(n_chunks);
+  const uint64_t P = payload_start(n_chunks);
+  uint8_t* payload = out + P;
+  unsigned long long* group_off = reinterpret_cast<unsigned long long*>(out + kIndexOff);
+  uint16_t* chunk_bits = reinterpret_cast<uint16_t*>(out + kIndexOff + 8 * n_groups);
+  const uint64_t group_syms = (uint64_t)kGroupChunks * cs;
+
+  while (true) {
+    __syncthreads();
+    if (tid == 0) s_group = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint64_t g = s_group;
+    if (g >= n_groups) break;
+    const uint64_t gbeg = g * group_syms;
+    const uint64_t gend = min(gbeg + group_syms, n);
+    if (g == 0) write_header(out, n, cs, n_chunks, lut, tid);
+
+    // ---- pass 1: bits of each chunk; warp w takes chunks w, w+8, ...
+    for (uint32_t c = warp; c < kGroupChunks; c += kEncWarps) {
+      const uint64_t cbeg = gbeg + (uint64_t)c * cs;
+      uint32_t bits = 0;
+      if (cbeg < gend) {
+        const uint32_t m = (uint32_t)(min(cbeg + cs, gend) - cbeg);
+        const uint32_t nv = m / 16;
+        const uint4* v = reinterpret_cast<const uint4*>(in + cbeg);
+        uint32_t k = lane;
+        for (; k + (kPass1Unroll - 1) * 32 < nv; k += kPass1Unroll * 32) {
+          uint4 q[kPass1Unroll];
+#pragma unroll
+          for (int u = 0; u < kPass1Unroll; u++) q[u] = ldg_nc_v4(v + k + 32 * u);
+#pragma unroll
+          for (int u = 0; u < kPass1Unroll; u++) bits += len16(s_len, q[u]);
+        }
+        for (; k < nv; k += 32) bits += len16(s_len, ldg_nc_v4(v + k));
+        for (uint32_t t = nv * 16 + lane; t < m; t += 32) bits += s_len[fold(in[cbeg + t])];
+        bits = warp_sum_u32(bits);
+        if (lane == 0) chunk_bits[g * kGroupChunks + c] = (uint16_t)bits;
+      }
+      if (lane == 0) s_chunk_bits[c] = bits;
+    }
+    __syncthreads();
+
+    // ---- look-back: this group's byte offset in the payload
+    if (warp == 0) {
+      const uint32_t gbits = warp_sum_u32(s_chunk_bits[lane]);
+      const uint64_t gbytes = align16((gbits + 7) / 8);
+      bool err = false;
+      const unsigned long long excl = lookback(gstat, g, gbytes, lane, &err);
+      if (lane == 0) {
+        s_excl = excl;
+        s_err = err;
+        if (err) {
+          set_status(status, QLC_ERR_TIMEOUT);
+        } else {
+          group_off[g] = excl;
+          if (g == n_groups - 1) {
+            *reinterpret_cast<unsigned long long*>(out + 48) = excl + gbytes;
+            *out_bytes = P + excl + gbytes;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (s_err) continue;
+    uint4* dst = reinterpret_cast<uint4*>(payload + s_excl);
+
+    // ---- pass 2: pack the group's codewords, tile by tile
+    uint32_t base_bit = 0;  // group-relative bit position of the tile start
+    uint32_t win = 0;       // group-relative word index of s_stage[0] (multiple of 4)
+    uint4 qn = make_uint4(0, 0, 0, 0);
+    {
+      const uint64_t my = gbeg + (uint64_t)tid * 16;
+      if (my + 16 <= gend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + my));
+    }
+    for (uint64_t tbeg = gbeg; tbeg < gend; tbeg += kTile) {
+      const uint64_t my = tbeg + (uint64_t)tid * 16;
+      uint4 q = qn;
+      int cnt = 16;
+      if (my + 16 > gend) {  // ragged end of the last group only
+        cnt = my < gend ? (int)(gend - my) : 0;
+        uint32_t w[4] = {0, 0, 0, 0};
+        for (int j = 0; j < cnt; j++) w[j >> 2] |= (uint32_t)in[my + j] << (8 * (j & 3));
+        q = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      {
+        const uint64_t nx = my + kTile;
+        if (nx + 16 <= gend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + nx));
+      }
+      uint32_t e[16];
+      uint32_t L = 0;
+      const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int j = 0; j < 16; j++) {
+        const uint32_t ent = s_enc[fold((qw[j >> 2] >> (8 * (j & 3))) & 0xFFu)];
+        e[j] = j < cnt ? ent : 0u;
+        L += e[j] & 15u;
+      }
+      // block exclusive scan of L
+      uint32_t incl = L;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) s_warp[warp] = incl;
+      __syncthreads();
+      uint32_t wpre = 0, total = 0;
+#pragma unroll
+      for (int w = 0; w < kEncWarps; w++) {
+        const uint32_t t = s_warp[w];
+        wpre += w < warp ? t : 0u;
+        total += t;
+      }
+      const uint32_t pos = base_bit + wpre + incl - L;
+      if (L) {
+        uint32_t wi = (pos >> 5) - win;
+        uint32_t nacc = pos & 31u;
+        unsigned long long acc = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+          acc |= ((unsigned long long)(e[j] & ~15u) << 32) >> nacc;
+          nacc += e[j] & 15u;
+          if (nacc >= 32) {
+            atomicOr(&s_stage[wi++], (uint32_t)(acc >> 32));
+            acc <<= 32;
+            nacc -= 32;
+          }
+        }
+        if (nacc) atomicOr(&s_stage[wi], (uint32_t)(acc >> 32));
+      }
+      __syncthreads();
+      const uint32_t end_bit = base_bit + total;
+      const uint32_t nblk = ((end_bit >> 5) - win) / 4;
+      for (uint32_t b = tid; b < nblk; b += kEncThreads) {
+        const uint32_t* s = &s_stage[4 * b];
+        dst[win / 4 + b] = make_uint4(bswap32(s[0]), bswap32(s[1]), bswap32(s[2]), bswap32(s[3]));
+      }
+      uint32_t carry = tid < 4 ? s_stage[4 * nblk + tid] : 0u;
+      __syncthreads();
+      const uint32_t used = 4 * nblk + 4;
+      for (uint32_t i = tid + 4; i < used; i += kEncThreads) s_stage[i] = 0;
+      if (tid < 4) s_stage[tid] = carry;
+      win += 4 * nblk;
+      base_bit = end_bit;
+      // (the next tile's first __syncthreads orders these writes)
+    }
+    __syncthreads();
+    // last, partial 16-byte block of the group (zero bits after the end)
+    if (tid == 0 && (base_bit & 127u)) {
+      const uint32_t* s = s_stage;
+      dst[win / 4] = make_uint4(bswap32(s[0]), bswap32(s[1]), bswap32(s[2]), bswap32(s[3]));
+    }
+    __syncthreads();
+    if (tid < 4) s_stage[tid] = 0;
+  }
+}
+
+// n = 0: a header-only container.
+__global__ void header_only_kernel(uint8_t* out, uint32_t cs, const qlc_lut* lut,
+                                   unsigned long long* out_bytes) {
+  const int tid = threadIdx.x;
+  write_header(out, 0, cs, 0, lut, tid);
+  if (tid == 0) {
+    *reinterpret_cast<unsigned long long*>(out + 48) = 0;
+    *out_bytes = payload_start(0);
+  }
+}
+
+}  // namespace qlc
+
+using namespace qlc;
+
+extern "C" {
+
+size_t qlc_encoded_size(size_t n, uint32_t chunk_symbols) {
+  if (!chunk_symbols_ok(chunk_symbols)) return 0;
+  const uint64_t n_chunks = (n + chunk_symbols - 1) / chunk_symbols;
+  const uint64_t group_syms = (uint64_t)kGroupChunks * chunk_symbols;
+  const uint64_t full = n / group_syms, rest = n % group_syms;
+  uint64_t total = payload_start(n_chunks);
+  total += full * align16((group_syms * kMaxCode + 7) / 8);
+  if (rest) total += align16((rest * kMaxCode + 7) / 8);
+  return (size_t)total;
+}
+
+size_t qlc_encode_workspace_size(size_t n, uint32_t chunk_symbols) {
+  if (!chunk_symbols_ok(chunk_symbols)) return 0;
+  const uint64_t n_chunks = (n + chunk_symbols - 1) / chunk_symbols;
+  return (size_t)(16 + 8 * n_groups_of(n_chunks));
+}
+
+qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint32_t chunk_symbols,
+                      uint8_t* d_out, size_t out_cap, void* d_ws, size_t ws_bytes,
+                      uint64_t* d_out_bytes, uint32_t* d_status, qlc_stream_t stream) {
+  if (!d_lut || !d_out || !d_out_bytes || (n > 0 && (!d_in || !d_ws))) return QLC_ERR_ARG;
+  if (!chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
+  if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0)
+    return QLC_ERR_ARG;
+  const uint64_t n_chunks = (n + chunk_symbols - 1) / chunk_symbols;
+  if (n_chunks > 0xFFFFFFFFull) return QLC_ERR_ARG;
+  if (out_cap < qlc_encoded_size(n, chunk_symbols)) return QLC_ERR_CAPACITY;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    header_only_kernel<<<1, 256, 0, st>>>(d_out, chunk_symbols, d_lut,
+                                          reinterpret_cast<unsigned long long*>(d_out_bytes));
+    return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+  }
+  const size_t ws_need = qlc_encode_workspace_size(n, chunk_symbols);
+  if (ws_bytes < ws_need) return QLC_ERR_CAPACITY;
+  if (cudaMemsetAsync(d_ws, 0, ws_need, st) != cudaSuccess) return QLC_ERR_CUDA;
+  const uint64_t n_groups = n_groups_of(n_chunks);
+  const uint64_t cap = (uint64_t)sm_count() * 2;
+  const int grid = (int)(n_groups < cap ? n_groups : cap);
+  unsigned int* ticket = static_cast<unsigned int*>(d_ws);
+  unsigned long long* gstat =
+      reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(d_ws) + 16);
+  encode_kernel<<<grid, kEncThreads, 0, st>>>(d_in, n, d_lut, chunk_symbols, d_out, ticket, gstat,
+                                              reinterpret_cast<unsigned long long*>(d_out_bytes),
+                                              d_status);
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+}  // extern "C"

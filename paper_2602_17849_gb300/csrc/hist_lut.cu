@@ -1,0 +1,269 @@
+// hist_lut.cu -- byte histogram (Section 4) and LUT construction (Section 7)
+// kernels of libqlc, plus their C-ABI entry points.
+#include "qlc_common.cuh"
+
+namespace qlc {
+
+constexpr int kHistWarps = 8;
+constexpr int kHistThreads = kHistWarps * 32;
+constexpr int kHistUnroll = 4;
+
+// Per-warp shared histograms, indexed with the bin's bit 7 folded into the
+// bank (b + (b >> 7)) so that a value and its negation (b, b ^ 0x80), which
+// are about equally frequent in sign-symmetric data, sit in different banks.
+__device__ __forceinline__ void count16(uint32_t* h, uint4 q) {
+  uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      uint32_t b = (w[k] >> (8 * j)) & 0xFFu;
+      atomicAdd(&h[b + (b >> 7)], 1u);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kHistThreads)
+hist_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __restrict__ hist) {
+  __shared__ uint32_t sh[kHistWarps][257];
+  for (int i = threadIdx.x; i < kHistWarps * 257; i += kHistThreads) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  uint32_t* my = sh[threadIdx.x >> 5];
+  const uint4* v = reinterpret_cast<const uint4*>(in);
+  const uint64_t nvec = n / 16;
+  const uint64_t stride = (uint64_t)gridDim.x * kHistThreads;
+  uint64_t i = (uint64_t)blockIdx.x * kHistThreads + threadIdx.x;
+  for (; i + (kHistUnroll - 1) * stride < nvec; i += kHistUnroll * stride) {
+    uint4 q[kHistUnroll];
+#pragma unroll
+    for (int u = 0; u < kHistUnroll; u++) q[u] = ldg_nc_v4(v + i + u * stride);
+#pragma unroll
+    for (int u = 0; u < kHistUnroll; u++) count16(my, q[u]);
+  }
+  for (; i < nvec; i += stride) count16(my, ldg_nc_v4(v + i));
+  if (blockIdx.x == 0) {
+    for (uint64_t t = nvec * 16 + threadIdx.x; t < n; t += kHistThreads) {
+      uint32_t b = in[t];
+      atomicAdd(&my[b + (b >> 7)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 256; b += kHistThreads) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kHistWarps; w++) s += sh[w][b + (b >> 7)];
+    if (s) atomicAdd(&hist[b], (unsigned long long)s);
+  }
+}
+
+// Rank of symbol s (Section 7): symbols with a larger count, or the same
+// count and a smaller value, come first.  256 threads, one per symbol; no
+// sort, each thread counts the symbols ahead of it.
+__device__ __forceinline__ int rank_of(const unsigned long long* h, int s) {
+  const unsigned long long c = h[s];
+  int r = 0;
+  for (int t = 0; t < 256; t++) {
+    const unsigned long long d = h[t];
+    r += (d > c) | ((d == c) & (t < s));
+  }
+  return r;
+}
+
+// Codeword of a rank under a scheme (Section 5): area code i, then the
+// rank's position in area i in area_bits[i] bits; 8-bit areas store the rank.
+__host__ __device__ inline uint32_t lut_entry(const qlc_scheme& sc, int r) {
+  uint32_t base = 0;
+  for (int i = 0; i < 8; i++) {
+    const uint32_t n = sc.area_n[i];
+    if ((uint32_t)r < base + n) {
+      const uint32_t b = sc.area_bits[i];
+      const uint32_t suffix = b == 8 ? (uint32_t)r : (uint32_t)r - base;
+      const uint32_t code = ((uint32_t)i << b) | suffix;
+      return (code << 4) | (3 + b);
+    }
+    base += n;
+  }
+  return 0;
+}
+
+__global__ void __launch_bounds__(256)
+lut_kernel(const unsigned long long* __restrict__ hist, qlc_scheme sc, qlc_lut* __restrict__ lut) {
+  __shared__ unsigned long long h[256];
+  const int s = threadIdx.x;
+  h[s] = hist[s];
+  __syncthreads();
+  const int r = rank_of(h, s);
+  lut->enc[s] = (uint16_t)lut_entry(sc, r);
+  lut->dec[r] = (uint8_t)s;
+  if (s < (int)(sizeof(qlc_scheme) / 4))
+    reinterpret_cast<uint32_t*>(&lut->scheme)[s] = reinterpret_cast<const uint32_t*>(&sc)[s];
+}
+
+struct SchemeSet {
+  qlc_scheme s[8];
+  int count;
+};
+
+// Section 6: the scheme can be adapted to the distribution.  Each candidate
+// is scored by its payload bits sum_s count[s] * len(rank[s]) and the
+// smallest wins (ties: the earlier candidate).
+__global__ void __launch_bounds__(256)
+lut_best_kernel(const unsigned long long* __restrict__ hist, SchemeSet set, qlc_lut* __restrict__ lut) {
+  __shared__ unsigned long long h[256];
+  __shared__ unsigned long long bits[8][8];
+  const int s = threadIdx.x;
+  h[s] = hist[s];
+  __syncthreads();
+  const int r = rank_of(h, s);
+  const int warp = s >> 5, lane = s & 31;
+  for (int k = 0; k < set.count; k++) {
+    unsigned long long v = h[s] * (unsigned long long)(lut_entry(set.s[k], r) & 15u);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) bits[k][warp] = v;
+  }
+  __syncthreads();
+  int best = 0;
+  unsigned long long best_bits = ~0ull;
+  for (int k = 0; k < set.count; k++) {
+    unsigned long long t = 0;
+    for (int w = 0; w < 8; w++) t += bits[k][w];
+    if (t < best_bits) {
+      best_bits = t;
+      best = k;
+    }
+  }
+  const qlc_scheme& sc = set.s[best];
+  lut->enc[s] = (uint16_t)lut_entry(sc, r);
+  lut->dec[r] = (uint8_t)s;
+  if (s < (int)(sizeof(qlc_scheme) / 4))
+    reinterpret_cast<uint32_t*>(&lut->scheme)[s] = reinterpret_cast<const uint32_t*>(&sc)[s];
+}
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
+  if (dev < 64 && cached[dev]) return cached[dev];
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+  if (dev < 64) cached[dev] = v;
+  return v;
+}
+
+}  // namespace qlc
+
+using namespace qlc;
+
+static const qlc_scheme kTable1 = {{8, 8, 8, 8, 8, 16, 32, 168}, {3, 3, 3, 3, 3, 4, 5, 8}, 1, {0}};
+static const qlc_scheme kTable2 = {{2, 8, 8, 8, 8, 32, 32, 158}, {1, 3, 3, 3, 3, 5, 5, 8}, 2, {0}};
+
+static bool scheme_valid(const qlc_scheme* s) {
+  if (!s || !scheme_ok(s->area_n, s->area_bits)) return false;
+  if (s->id == 1 || s->id == 2) {
+    const qlc_scheme& t = s->id == 1 ? kTable1 : kTable2;
+    for (int i = 0; i < 8; i++)
+      if (t.area_n[i] != s->area_n[i] || t.area_bits[i] != s->area_bits[i]) return false;
+  } else if (s->id != 0) {
+    return false;
+  }
+  return true;
+}
+
+static qlc_scheme clean_scheme(const qlc_scheme* s) {
+  qlc_scheme c = *s;
+  for (int i = 0; i < 7; i++) c.reserved[i] = 0;
+  return c;
+}
+
+extern "C" {
+
+int qlc_version(void) { return QLC_VERSION; }
+
+const char* qlc_status_string(qlc_status s) {
+  switch (s) {
+    case QLC_OK: return "ok";
+    case QLC_ERR_ARG: return "invalid argument";
+    case QLC_ERR_CAPACITY: return "buffer too small";
+    case QLC_ERR_CORRUPT: return "corrupt container";
+    case QLC_ERR_TIMEOUT: return "device wait timed out";
+    case QLC_ERR_CUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+qlc_status qlc_scheme_table(int id, qlc_scheme* out) {
+  if (!out || (id != 1 && id != 2)) return QLC_ERR_ARG;
+  *out = id == 1 ? kTable1 : kTable2;
+  return QLC_OK;
+}
+
+int qlc_scheme_check(const qlc_scheme* s) { return scheme_valid(s) ? 1 : 0; }
+
+qlc_status qlc_histogram(const uint8_t* d_in, size_t n, uint64_t* d_hist, int accumulate,
+                         qlc_stream_t stream) {
+  if (!d_hist || (n > 0 && !d_in)) return QLC_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_in) & 15u) != 0) return QLC_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!accumulate && cudaMemsetAsync(d_hist, 0, 256 * sizeof(uint64_t), st) != cudaSuccess)
+    return QLC_ERR_CUDA;
+  if (n == 0) return QLC_OK;
+  const uint64_t nvec = n / 16;
+  uint64_t want = (nvec + kHistThreads - 1) / kHistThreads;
+  uint64_t cap = (uint64_t)sm_count() * 6;
+  int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
+  hist_kernel<<<grid, kHistThreads, 0, st>>>(d_in, n, reinterpret_cast<unsigned long long*>(d_hist));
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+qlc_status qlc_build_lut(const uint64_t* d_hist, const qlc_scheme* h_scheme, qlc_lut* d_lut,
+                         qlc_stream_t stream) {
+  if (!d_hist || !d_lut || !scheme_valid(h_scheme)) return QLC_ERR_ARG;
+  lut_kernel<<<1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const unsigned long long*>(d_hist), clean_scheme(h_scheme), d_lut);
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+qlc_status qlc_build_lut_best(const uint64_t* d_hist, const qlc_scheme* h_schemes, int n_schemes,
+                              qlc_lut* d_lut, qlc_stream_t stream) {
+  if (!d_hist || !d_lut || !h_schemes || n_schemes < 1 || n_schemes > 8) return QLC_ERR_ARG;
+  SchemeSet set;
+  set.count = n_schemes;
+  for (int k = 0; k < n_schemes; k++) {
+    if (!scheme_valid(&h_schemes[k])) return QLC_ERR_ARG;
+    set.s[k] = clean_scheme(&h_schemes[k]);
+  }
+  lut_best_kernel<<<1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const unsigned long long*>(d_hist), set, d_lut);
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+qlc_status qlc_build_lut_host(const uint64_t* h_hist, const qlc_scheme* h_scheme, qlc_lut* h_lut) {
+  if (!h_hist || !h_lut || !scheme_valid(h_scheme)) return QLC_ERR_ARG;
+  h_lut->scheme = clean_scheme(h_scheme);
+  for (int s = 0; s < 256; s++) {
+    int r = 0;
+    for (int t = 0; t < 256; t++) r += (h_hist[t] > h_hist[s]) || (h_hist[t] == h_hist[s] && t < s);
+    h_lut->enc[s] = (uint16_t)lut_entry(h_lut->scheme, r);
+    h_lut->dec[r] = (uint8_t)s;
+  }
+  return QLC_OK;
+}
+
+qlc_status qlc_peek_header(const void* h_hdr, size_t hdr_bytes, uint64_t* n, uint64_t* container_bytes) {
+  if (!h_hdr || hdr_bytes < QLC_HEADER_BYTES) return QLC_ERR_ARG;
+  const uint8_t* p = static_cast<const uint8_t*>(h_hdr);
+  auto le = [&](int off, int bytes) {
+    uint64_t v = 0;
+    for (int i = 0; i < bytes; i++) v |= (uint64_t)p[off + i] << (8 * i);
+    return v;
+  };
+  if (p[0] != 'Q' || p[1] != 'L' || p[2] != 'C' || p[3] != '1' || le(4, 2) != QLC_VERSION)
+    return QLC_ERR_CORRUPT;
+  const uint64_t nn = le(8, 8);
+  const uint64_t n_chunks = le(20, 4);
+  if (n) *n = nn;
+  if (container_bytes) *container_bytes = payload_start(n_chunks) + le(48, 8);
+  return QLC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// qlc_common.cuh -- shared definitions of the libqlc CUDA kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qlc.h"
+
+namespace qlc {
+
+constexpr uint32_t kGroupChunks = QLC_CHUNKS_PER_GROUP;  // chunks per group
+constexpr uint32_t kIndexOff = QLC_INDEX_OFFSET;         // header 64 + dec 256
+constexpr uint32_t kMaxCode = 11;                        // 3 + 8 suffix bits
+
+__host__ __device__ __forceinline__ uint64_t align16(uint64_t v) {
+  return (v + 15u) & ~uint64_t(15);
+}
+__host__ __device__ __forceinline__ uint64_t n_groups_of(uint64_t n_chunks) {
+  return (n_chunks + kGroupChunks - 1) / kGroupChunks;
+}
+__host__ __device__ __forceinline__ uint64_t payload_start(uint64_t n_chunks) {
+  return align16(kIndexOff + 8 * n_groups_of(n_chunks) + 2 * n_chunks);
+}
+__host__ __device__ __forceinline__ bool chunk_symbols_ok(uint64_t cs) {
+  return cs >= QLC_MIN_CHUNK && cs <= QLC_MAX_CHUNK && cs % 128 == 0;
+}
+
+// Scheme validity (qlc.h): counts sum to 256, widths never decrease, an area
+// with b < 8 bits is complete (2^b ranks), an 8-bit area holds 1..256 ranks.
+__host__ __device__ inline bool scheme_ok(const uint16_t n[8], const uint8_t b[8]) {
+  uint32_t total = 0;
+  for (int i = 0; i < 8; i++) {
+    if (b[i] > 8) return false;
+    if (i > 0 && b[i] < b[i - 1]) return false;
+    if (b[i] < 8) {
+      if (n[i] != (1u << b[i])) return false;
+    } else if (n[i] < 1 || n[i] > 256) {
+      return false;
+    }
+    total += n[i];
+  }
+  return total == 256;
+}
+
+// First error wins.
+__device__ __forceinline__ void set_status(uint32_t* st, uint32_t code) {
+  if (st) atomicCAS(st, 0u, code);
+}
+
+// Big-endian view of a little-endian 32-bit word: byte 0 becomes bits 31..24,
+// so the first bit of the stream is the word's most significant bit.
+__device__ __forceinline__ uint32_t bswap32(uint32_t w) { return __byte_perm(w, 0, 0x0123); }
+
+__device__ __forceinline__ uint4 ldg_nc_v4(const uint4* p) {
+  uint4 r;
+  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p));
+  return r;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+}  // namespace qlc

@@ -1,0 +1,276 @@
+"""Python binding of libqlc (include/qlc.h): argument marshalling only.
+
+Every entry point of the C ABI is exposed under the same name and takes
+PyTorch tensors for device buffers (uint8 / int64 views of device memory) and
+the current CUDA stream.  All compute runs in the library's CUDA kernels; if
+libqlc.so is missing or fails to load, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA = range(6)
+CHUNKS_PER_GROUP = 32
+HEADER_BYTES = 64
+INDEX_OFFSET = 320
+LUT_BYTES = 800
+SCHEME_BYTES = 32
+
+
+class QlcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+class qlc_scheme(ctypes.Structure):
+    _fields_ = [("area_n", ctypes.c_uint16 * 8), ("area_bits", ctypes.c_uint8 * 8),
+                ("id", ctypes.c_uint8), ("reserved", ctypes.c_uint8 * 7)]
+
+
+class qlc_lut(ctypes.Structure):
+    _fields_ = [("scheme", qlc_scheme), ("enc", ctypes.c_uint16 * 256), ("dec", ctypes.c_uint8 * 256)]
+
+
+assert ctypes.sizeof(qlc_scheme) == SCHEME_BYTES and ctypes.sizeof(qlc_lut) == LUT_BYTES
+
+
+def _load() -> ctypes.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libqlc.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    P, sz, u32, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_int
+    L.qlc_version.restype = i32
+    L.qlc_status_string.argtypes = [i32]
+    L.qlc_status_string.restype = ctypes.c_char_p
+    L.qlc_scheme_table.argtypes = [i32, P]
+    L.qlc_scheme_check.argtypes = [P]
+    L.qlc_histogram.argtypes = [P, sz, P, i32, P]
+    L.qlc_build_lut.argtypes = [P, P, P, P]
+    L.qlc_build_lut_host.argtypes = [P, P, P]
+    L.qlc_build_lut_best.argtypes = [P, P, i32, P, P]
+    L.qlc_encoded_size.argtypes = [sz, u32]
+    L.qlc_encoded_size.restype = sz
+    L.qlc_encode_workspace_size.argtypes = [sz, u32]
+    L.qlc_encode_workspace_size.restype = sz
+    L.qlc_encode.argtypes = [P, sz, P, u32, P, sz, P, sz, P, P, P]
+    L.qlc_decode.argtypes = [P, sz, P, sz, P, P, P]
+    L.qlc_peek_header.argtypes = [P, sz, P, P]
+    for f in ("qlc_scheme_table", "qlc_histogram", "qlc_build_lut", "qlc_build_lut_host",
+              "qlc_build_lut_best", "qlc_encode", "qlc_decode", "qlc_peek_header"):
+        getattr(L, f).restype = i32
+    return L
+
+
+lib = _load()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    return int(t.data_ptr())
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise QlcError(st, what)
+
+
+def _nbytes(t: torch.Tensor) -> int:
+    return t.numel() * t.element_size()
+
+
+# ----------------------------------------------------------------- C ABI names
+
+def qlc_version() -> int:
+    return int(lib.qlc_version())
+
+
+def status_string(st: int) -> str:
+    return lib.qlc_status_string(int(st)).decode()
+
+
+qlc_status_string = status_string
+
+
+def qlc_scheme_table(scheme_id: int) -> qlc_scheme:
+    s = qlc_scheme()
+    _check(lib.qlc_scheme_table(int(scheme_id), ctypes.byref(s)), "qlc_scheme_table")
+    return s
+
+
+def make_scheme(area_n, area_bits, scheme_id: int = 0) -> qlc_scheme:
+    s = qlc_scheme()
+    for i in range(8):
+        s.area_n[i] = int(area_n[i])
+        s.area_bits[i] = int(area_bits[i])
+    s.id = int(scheme_id)
+    return s
+
+
+def as_scheme(scheme) -> qlc_scheme:
+    if isinstance(scheme, qlc_scheme):
+        return scheme
+    if isinstance(scheme, int):
+        return qlc_scheme_table(scheme)
+    n, b = scheme[0], scheme[1]
+    return make_scheme(n, b, scheme[2] if len(scheme) > 2 else 0)
+
+
+def qlc_scheme_check(scheme) -> bool:
+    s = as_scheme(scheme)
+    return bool(lib.qlc_scheme_check(ctypes.byref(s)))
+
+
+def qlc_histogram(d_in: torch.Tensor, d_hist: torch.Tensor, accumulate: bool = False,
+                  n: int | None = None, stream=None) -> torch.Tensor:
+    """d_in: CUDA uint8; d_hist: CUDA int64[256] (uint64 counts)."""
+    n = _nbytes(d_in) if n is None else n
+    _check(lib.qlc_histogram(_ptr(d_in), n, _ptr(d_hist), int(bool(accumulate)), _stream(stream)),
+           "qlc_histogram")
+    return d_hist
+
+
+def qlc_build_lut(d_hist: torch.Tensor, scheme, d_lut: torch.Tensor, stream=None) -> torch.Tensor:
+    """d_lut: CUDA uint8[800] receiving a qlc_lut."""
+    s = as_scheme(scheme)
+    _check(lib.qlc_build_lut(_ptr(d_hist), ctypes.byref(s), _ptr(d_lut), _stream(stream)),
+           "qlc_build_lut")
+    return d_lut
+
+
+def qlc_build_lut_best(d_hist: torch.Tensor, schemes, d_lut: torch.Tensor, stream=None) -> torch.Tensor:
+    arr = (qlc_scheme * len(schemes))(*[as_scheme(s) for s in schemes])
+    _check(lib.qlc_build_lut_best(_ptr(d_hist), arr, len(schemes), _ptr(d_lut), _stream(stream)),
+           "qlc_build_lut_best")
+    return d_lut
+
+
+def qlc_build_lut_host(hist, scheme) -> qlc_lut:
+    h = (ctypes.c_uint64 * 256)(*[int(v) for v in hist])
+    s = as_scheme(scheme)
+    out = qlc_lut()
+    _check(lib.qlc_build_lut_host(h, ctypes.byref(s), ctypes.byref(out)), "qlc_build_lut_host")
+    return out
+
+
+def qlc_encoded_size(n: int, chunk_symbols: int = 4096) -> int:
+    return int(lib.qlc_encoded_size(int(n), int(chunk_symbols)))
+
+
+def qlc_encode_workspace_size(n: int, chunk_symbols: int = 4096) -> int:
+    return int(lib.qlc_encode_workspace_size(int(n), int(chunk_symbols)))
+
+
+def qlc_encode(d_in: torch.Tensor, d_lut: torch.Tensor, chunk_symbols: int, d_out: torch.Tensor,
+               d_ws: torch.Tensor, d_out_bytes: torch.Tensor, d_status: torch.Tensor,
+               n: int | None = None, stream=None) -> None:
+    n = _nbytes(d_in) if n is None else n
+    _check(lib.qlc_encode(_ptr(d_in), n, _ptr(d_lut), int(chunk_symbols), _ptr(d_out), _nbytes(d_out),
+                          _ptr(d_ws), _nbytes(d_ws) if d_ws is not None else 0, _ptr(d_out_bytes),
+                          _ptr(d_status), _stream(stream)), "qlc_encode")
+
+
+def qlc_decode(d_in: torch.Tensor, d_out: torch.Tensor, d_n_out: torch.Tensor, d_status: torch.Tensor,
+               in_bytes: int | None = None, out_cap: int | None = None, stream=None) -> None:
+    in_bytes = _nbytes(d_in) if in_bytes is None else in_bytes
+    out_cap = _nbytes(d_out) if out_cap is None else out_cap
+    _check(lib.qlc_decode(_ptr(d_in), in_bytes, _ptr(d_out), out_cap, _ptr(d_n_out), _ptr(d_status),
+                          _stream(stream)), "qlc_decode")
+
+
+def qlc_peek_header(hdr: bytes):
+    buf = ctypes.create_string_buffer(bytes(hdr), len(hdr))
+    n = ctypes.c_uint64()
+    c = ctypes.c_uint64()
+    _check(lib.qlc_peek_header(buf, len(hdr), ctypes.byref(n), ctypes.byref(c)), "qlc_peek_header")
+    return int(n.value), int(c.value)
+
+
+# ------------------------------------------------------------ conveniences
+
+class Codec:
+    """Device buffers for encoding/decoding tensors of up to `max_n` symbols.
+
+    All buffers are allocated once (PyTorch caching allocator) and reused;
+    encode() and decode() launch only the library's kernels.
+    """
+
+    def __init__(self, max_n: int, chunk_symbols: int = 4096, scheme=1, device="cuda"):
+        self.device = torch.device(device)
+        self.chunk_symbols = int(chunk_symbols)
+        self.max_n = int(max_n)
+        self.scheme = scheme
+        cap = qlc_encoded_size(self.max_n, self.chunk_symbols)
+        if cap == 0:
+            raise QlcError(ERR_ARG, "chunk_symbols")
+        z = dict(device=self.device)
+        self.cap = cap
+        self.hist = torch.zeros(256, dtype=torch.int64, **z)
+        self.lut = torch.zeros(LUT_BYTES, dtype=torch.uint8, **z)
+        self.ws = torch.zeros(max(16, qlc_encode_workspace_size(self.max_n, self.chunk_symbols)),
+                              dtype=torch.uint8, **z)
+        self.out_bytes = torch.zeros(1, dtype=torch.int64, **z)
+        self.n_out = torch.zeros(1, dtype=torch.int64, **z)
+        self.status = torch.zeros(1, dtype=torch.int32, **z)
+
+    def new_container(self) -> torch.Tensor:
+        return torch.empty(self.cap, dtype=torch.uint8, device=self.device)
+
+    def encode_into(self, x: torch.Tensor, out: torch.Tensor, stream=None, build_lut: bool = True) -> None:
+        """Histogram -> LUT (self.scheme, or the best of a list) -> container."""
+        n = x.numel()
+        if build_lut:
+            qlc_histogram(x, self.hist, n=n, stream=stream)
+            if isinstance(self.scheme, list):  # several candidates: the best for this histogram
+                qlc_build_lut_best(self.hist, self.scheme, self.lut, stream=stream)
+            else:
+                qlc_build_lut(self.hist, self.scheme, self.lut, stream=stream)
+        qlc_encode(x, self.lut, self.chunk_symbols, out, self.ws, self.out_bytes, self.status,
+                   n=n, stream=stream)
+
+    def decode_into(self, container: torch.Tensor, out: torch.Tensor, stream=None,
+                    in_bytes: int | None = None) -> None:
+        qlc_decode(container, out, self.n_out, self.status, in_bytes=in_bytes, stream=stream)
+
+    def check(self) -> None:
+        st = int(self.status.item())
+        if st != OK:
+            self.status.zero_()
+            raise QlcError(st, "device")
+
+
+def encode(x: torch.Tensor, scheme=1, chunk_symbols: int = 4096) -> torch.Tensor:
+    """Container of a CUDA uint8 tensor, trimmed to its size (synchronises)."""
+    codec = Codec(max(x.numel(), 1), chunk_symbols, scheme, x.device)
+    out = codec.new_container()
+    codec.encode_into(x.reshape(-1), out)
+    codec.check()
+    return out[: int(codec.out_bytes.item())]
+
+
+def decode(container: torch.Tensor) -> torch.Tensor:
+    """Decoded bytes of a CUDA container (synchronises to size the output)."""
+    n, total = qlc_peek_header(container[:HEADER_BYTES].cpu().numpy().tobytes())
+    out = torch.empty(max(n, 1), dtype=torch.uint8, device=container.device)
+    n_out = torch.zeros(1, dtype=torch.int64, device=container.device)
+    status = torch.zeros(1, dtype=torch.int32, device=container.device)
+    qlc_decode(container, out, n_out, status, out_cap=n)
+    st = int(status.item())
+    if st != OK:
+        raise QlcError(st, "qlc_decode")
+    return out[:n]
