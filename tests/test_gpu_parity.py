@@ -143,7 +143,7 @@ def test_build_lut_best_picks_fewer_bits(qlc):
         lut = torch.zeros(800, dtype=torch.uint8, device="cuda")
         qlc.qlc_build_lut_best(hd, [1, 2], lut)
         lb = lut.cpu().numpy()
-        assert lb[16] == best                          # qlc_scheme.id
+        assert lb[24] == best                          # qlc_scheme.id
         _check_lut(lb, h, best)
 
 
