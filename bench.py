@@ -199,6 +199,7 @@ def main():
     from paper_2602_17849_gb300 import inputs, qlc
 
     x = inputs.make_e4m3("t4", N_BYTES, seed=rank, device=dev)
+    torch.cuda.empty_cache()  # drop the generator's temporaries
     codec = qlc.Codec(N_BYTES, CHUNK, SCHEME, dev)
     cont = codec.new_container()
     y = torch.empty(N_BYTES, dtype=torch.uint8, device=dev)
