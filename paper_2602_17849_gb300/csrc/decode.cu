@@ -3,21 +3,23 @@
 // One warp per group of 32 chunks, one lane per chunk: the codes are not
 // self-synchronising, so each lane starts at its chunk's bit offset (group
 // offset + exclusive scan of the group's chunk_bits) and decodes its chunk
-// serially.  Per symbol: a 32-bit window at the bit offset; its top 3 bits are
-// the area code; the code length 3 + bits[area] comes from a byte permute of
-// two registers (no memory access on the serial path); the whole codeword
-// (area code and suffix, right-aligned) indexes a 2048-entry code -> symbol
-// table in shared memory built from the LUT and the area table.  The rank is
-// never formed explicitly: for every code of every area the table holds
+// serially.  Per symbol: the top 3 bits of a 64-bit bit buffer are the area
+// code; the code length 3 + bits[area] comes from a byte permute of two
+// registers (no memory access on the serial path); the whole codeword (area
+// code and suffix, right-aligned) indexes a 2048-entry code -> symbol table in
+// shared memory built from the LUT and the area table.  The rank is never
+// formed explicitly: for every code of every area the table holds
 // dec[offset + suffix] (offset 0 for 8-bit areas), exactly the paper's rule.
-// Input: 16-byte vector loads per lane, two vectors of prefetch.  Output:
-// 16 symbols per shared-memory store into a swizzled 32 x 128-byte tile; every
-// 128 symbols the warp writes the tile out as 128-byte row segments.
+// Input: each lane's chunk bytes stream through a 128-byte shared-memory ring
+// filled by cp.async; the buffer is refilled one word per two symbols under
+// predication, so lanes never diverge.  Output: 16 symbols per shared store
+// into a swizzled 32 x 32-byte tile; every 32 symbols the warp writes the tile
+// out, one 32-byte segment per chunk.
 #include "qlc_common.cuh"
 
 namespace qlc {
 
-constexpr int kDecCtasPerSm = 16;
+constexpr int kDecCtasPerSm = 26;  // 26 x (7.4 KB + 1 KB reserved) fits in 228 KB
 
 struct DecHeader {
   uint64_t n, payload_bytes, P, n_chunks, n_groups;
@@ -79,69 +81,121 @@ __device__ uint32_t parse_header(const uint8_t* in, uint64_t in_bytes, uint64_t 
   return 0;
 }
 
-// Per-lane bit reader over a group's payload: a 64-bit window (w0:w1) with
-// bit offset o into w0, the rest of the current 16-byte vector (a, b, c) and
-// two prefetched vectors.
-struct Reader {
-  uint32_t w0, w1, o;
-  uint32_t a, b, c;
-  int left;  // words of the current vector not yet moved into the window
-  uint4 n1, n2;
-  const uint4* vp;
-  const uint4* vend;
-  uint32_t shifted;  // words shifted out of the window so far
+// cp.async (global -> shared, 16 bytes, bypassing L1) and its groups.
+__device__ __forceinline__ void cp_async16(uint32_t smem, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
-  __device__ __forceinline__ uint4 fetch() {
-    uint4 r = make_uint4(0, 0, 0, 0);
-    if (vp < vend) r = ldg_nc_v4(vp);
-    vp++;
-    return r;
+constexpr uint32_t kBlk = 32;       // symbols per lane between output flushes
+constexpr uint32_t kRingVec = 8;    // 16-byte vectors in each lane's input ring (128 B)
+
+// (hi * 8) >> 32 + c, i.e. (hi >> 29) + c, on the multiply-add pipe.
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+// prmt.b32 in its default mode; a selector nibble with bit 3 set yields the
+// sign of the selected byte replicated (0x00 for bytes below 0x80).
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
+}
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+// 0x80000000 >> s with PTX semantics (0 for s >= 32).
+__device__ __forceinline__ uint32_t top_bit_shr(uint32_t s) {
+  uint32_t d;
+  asm("shr.b32 %0, %1, %2;" : "=r"(d) : "r"(0x80000000u), "r"(s));
+  return d;
+}
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+
+// Per-lane decoder state.  Input: the lane's chunk bytes are copied 16 bytes
+// at a time (cp.async) into a 128-byte ring in shared memory, ahead of use.
+// Bits: a 64-bit buffer (hi:lo) of valid bits, most significant first, with
+// nb1 = (valid bits - 1).  Two symbols (at most 2 x 11 bits) are decoded per
+// round with no branch; then one 32-bit word is inserted, under predication,
+// when at most 32 bits are left, which keeps at least 32 valid bits at the
+// start of every round.
+struct LaneDec {
+  uint32_t hi, lo;
+  uint32_t nb1;
+  uint32_t rpb;  // byte offset (group-relative) of the next word to insert
+  uint32_t nxt;  // that word, already read from the ring
+  uint32_t fv;   // next 16-byte vector to fetch (group-relative)
+  uint32_t vend; // vectors in the group
+  const uint4* gp;
+  uint32_t ring_s;  // shared address of this lane's ring (128-byte aligned)
+
+  // Fetch vectors up to the ring's capacity past the read position, never
+  // past the group end, and commit them as one cp.async group.
+  __device__ __forceinline__ void fetch() {
+    const uint32_t want = min((rpb >> 4) + kRingVec, vend);
+    for (; fv < want; fv++) cp_async16(ring_s + (fv % kRingVec) * 16, gp + fv);
+    cp_async_commit();
   }
-  __device__ __forceinline__ uint32_t pop() {
-    uint32_t r;
-    if (left == 0) {
-      r = bswap32(n1.x);
-      a = bswap32(n1.y);
-      b = bswap32(n1.z);
-      c = bswap32(n1.w);
-      left = 3;
-      n1 = n2;
-      n2 = fetch();
-    } else {
-      r = a;
-      a = b;
-      b = c;
-      left--;
+  __device__ __forceinline__ uint32_t ring_word(uint32_t byte_off) const {
+    // ring_s is 128-byte aligned, so OR places the offset inside the ring
+    return bswap32(ld_shared_u32(ring_s | (byte_off & (kRingVec * 16 - 1))));
+  }
+  // Code length of the codeword at the top of x (Section 7: the area code,
+  // i.e. the top 3 bits, fixes it): a byte permute of two registers; the
+  // selector's sign-mode nibbles make bytes 1-3 zero.
+  __device__ __forceinline__ static uint32_t code_len(uint32_t x, uint32_t len_lo, uint32_t len_hi) {
+    return prmt(len_lo, len_hi, mad_hi(x, 8u, 0x8880u));
+  }
+  // Insert the next word below the valid bits when at most 32 remain:
+  // q = 2^(32 - valid), or 0 when no word is due, so the insertion is two
+  // multiply-adds with no select.
+  __device__ __forceinline__ void refill() {
+    const uint32_t q = top_bit_shr(nb1);
+    hi = mad_hi(nxt, q, hi);  // nxt >> valid
+    lo = mad_lo(nxt, q, lo);  // nxt << (32 - valid)
+    if (nb1 < 32) {
+      nb1 += 32;
+      rpb += 4;
+      nxt = ring_word(rpb);
     }
-    return r;
   }
-  __device__ __forceinline__ void init(const uint4* vbase, uint64_t S, uint64_t vend_idx) {
-    vend = vbase + vend_idx;
-    vp = vbase + (S >> 7);
-    left = 0;
-    n1 = fetch();
-    n2 = fetch();
-    const int skip = (int)((S >> 5) & 3);
-    for (int k = 0; k < skip; k++) pop();
-    w0 = pop();
-    w1 = pop();
-    o = (uint32_t)(S & 31);
-    shifted = 0;
+  // Two symbols (at most 22 bits) from the top of the buffer, packed as
+  // s0 | s1 << 8; the buffer advances once by both lengths.
+  __device__ __forceinline__ uint32_t round2(const uint8_t* T, uint32_t len_lo, uint32_t len_hi) {
+    const uint32_t la = code_len(hi, len_lo, len_hi);
+    const uint32_t a = T[__funnelshift_l(hi, 0u, la)];
+    const uint32_t h1 = __funnelshift_l(lo, hi, la);
+    const uint32_t lb = code_len(h1, len_lo, len_hi);
+    const uint32_t b = T[__funnelshift_l(h1, 0u, lb)];
+    const uint32_t lab = la + lb;
+    hi = __funnelshift_l(lo, hi, lab);
+    lo <<= lab;
+    nb1 -= lab;
+    refill();
+    return mad_lo(b, 256u, a);
   }
-  // One symbol (Section 7): area code -> code length; codeword -> symbol.
-  __device__ __forceinline__ uint32_t next(const uint8_t* T, uint32_t len_lo, uint32_t len_hi) {
-    const uint32_t x = __funnelshift_l(w1, w0, o);
-    const uint32_t len = __byte_perm(len_lo, len_hi, x >> 29) & 0xFFu;
-    const uint32_t code = __funnelshift_l(x, 0u, len);
-    const uint32_t sym = T[code];
-    o += len;
-    if (o >= 32) {
-      o -= 32;
-      w0 = w1;
-      w1 = pop();
-      shifted++;
-    }
-    return sym;
+  // One symbol with a refill (ragged chunk ends only).
+  __device__ __forceinline__ uint32_t round1(const uint8_t* T, uint32_t len_lo, uint32_t len_hi) {
+    const uint32_t la = code_len(hi, len_lo, len_hi);
+    const uint32_t a = T[__funnelshift_l(hi, 0u, la)];
+    hi = __funnelshift_l(lo, hi, la);
+    lo <<= la;
+    nb1 -= la;
+    refill();
+    return a;
   }
 };
 
@@ -149,7 +203,9 @@ __global__ void __launch_bounds__(32, kDecCtasPerSm)
 decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __restrict__ out,
               uint64_t out_cap, unsigned long long* __restrict__ n_out, uint32_t* __restrict__ status) {
   __shared__ __align__(16) uint8_t s_T[2048];
-  __shared__ __align__(16) uint4 s_rows[32 * 8];
+  __shared__ __align__(128) uint4 s_ring[32 * kRingVec];
+  __shared__ __align__(16) uint4 s_tile[32 * (kBlk / 16)];
+  __shared__ __align__(16) uint8_t s_dec[256];
   __shared__ uint32_t s_seen[8];
   const int lane = threadIdx.x;
 
@@ -165,15 +221,16 @@ decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __rest
   if (blockIdx.x == 0 && lane == 0) *n_out = h.n;
   if (blockIdx.x >= h.n_groups) return;
 
-  // code -> symbol table: every code (i << bits[i]) | s of every area i
+  // code -> symbol table: every code (i << bits[i]) | s of every area i maps
+  // to dec[offset_i + s] (offset 0 for 8-bit areas); dec staged in shared.
+  reinterpret_cast<uint32_t*>(s_dec)[lane] = reinterpret_cast<const uint32_t*>(in + 64)[lane];
+  reinterpret_cast<uint32_t*>(s_dec)[lane + 32] = reinterpret_cast<const uint32_t*>(in + 64)[lane + 32];
+  __syncwarp();
   {
     uint32_t base = 0;
     for (int i = 0; i < 8; i++) {
       const uint32_t b = in[40 + i];
-      for (uint32_t s = lane; s < (1u << b); s += 32) {
-        const uint32_t rank = b == 8 ? s : base + s;
-        s_T[(i << b) | s] = in[64 + rank];
-      }
+      for (uint32_t s = lane; s < (1u << b); s += 32) s_T[(i << b) | s] = s_dec[b == 8 ? s : base + s];
       base += *reinterpret_cast<const uint16_t*>(in + 24 + 2 * i);
     }
   }
@@ -183,6 +240,13 @@ decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __rest
   const uint16_t* chunk_bits = reinterpret_cast<const uint16_t*>(in + kIndexOff + 8 * h.n_groups);
   const uint4* vbase = reinterpret_cast<const uint4*>(in + h.P);
   const uint32_t cs = h.cs;
+  const uint32_t len_lo = h.len_lo, len_hi = h.len_hi;
+  LaneDec d;
+  d.ring_s = (uint32_t)__cvta_generic_to_shared(&s_ring[lane * kRingVec]);
+  if (__cvta_generic_to_shared(s_ring) & 127u) {  // the ring addressing relies on it
+    if (lane == 0) set_status(status, QLC_ERR_CUDA);
+    return;
+  }
 
   for (uint64_t g = blockIdx.x; g < h.n_groups; g += gridDim.x) {
     const uint64_t c = g * kGroupChunks + lane;
@@ -204,65 +268,81 @@ decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __rest
       if (lane == 0) set_status(status, QLC_ERR_CORRUPT);
       continue;
     }
-    const uint64_t S = goff * 8 + (incl - bits);
-    Reader rd;
-    rd.init(vbase, S, gnext / 16);
-    const uint32_t nmax = __reduce_max_sync(0xffffffffu, nsym);
+    // lane start bit (group-relative), ring fill, buffer fill
+    const uint32_t S = incl - bits;
+    d.gp = vbase + goff / 16;
+    d.vend = (uint32_t)((gnext - goff) / 16);
+    d.fv = S >> 7;
+    d.rpb = (S >> 5) * 4;
+    d.fetch();
+    cp_async_wait<0>();
+    d.hi = d.ring_word(d.rpb);
+    d.lo = d.ring_word(d.rpb + 4);
+    d.rpb += 8;
+    d.nxt = d.ring_word(d.rpb);
+    {
+      const uint32_t o = S & 31u;
+      d.hi = __funnelshift_l(d.lo, d.hi, o);
+      d.lo <<= o;
+      d.nb1 = 63u - o;
+    }
 
-    for (uint32_t i0 = 0; i0 < nmax; i0 += 128) {
-      const uint32_t cnt = nsym > i0 ? min(128u, nsym - i0) : 0u;
-      if (cnt == 128) {
-#pragma unroll 1
-        for (int k = 0; k < 8; k++) {
+    const uint32_t nmax = __reduce_max_sync(0xffffffffu, nsym);
+    for (uint32_t i0 = 0; i0 < nmax; i0 += kBlk) {
+      d.fetch();
+      cp_async_wait<1>();
+      const uint32_t cnt = nsym > i0 ? min(kBlk, nsym - i0) : 0u;
+      if (cnt == kBlk) {
+#pragma unroll
+        for (int k = 0; k < (int)(kBlk / 16); k++) {
           uint32_t w[4];
 #pragma unroll
           for (int j = 0; j < 4; j++) {
-            uint32_t v = rd.next(s_T, h.len_lo, h.len_hi);
-            v |= rd.next(s_T, h.len_lo, h.len_hi) << 8;
-            v |= rd.next(s_T, h.len_lo, h.len_hi) << 16;
-            v |= rd.next(s_T, h.len_lo, h.len_hi) << 24;
-            w[j] = v;
+            const uint32_t p0 = d.round2(s_T, len_lo, len_hi);
+            const uint32_t p1 = d.round2(s_T, len_lo, len_hi);
+            w[j] = __byte_perm(p0, p1, 0x5410);
           }
-          s_rows[lane * 8 + (k ^ (lane & 7))] = make_uint4(w[0], w[1], w[2], w[3]);
+          s_tile[lane * 2 + (k ^ ((lane >> 2) & 1))] = make_uint4(w[0], w[1], w[2], w[3]);
         }
       } else if (cnt > 0) {
-        for (int k = 0; k < 8; k++) {
+        for (int k = 0; k < (int)(kBlk / 16); k++) {
           uint32_t w[4];
 #pragma unroll
           for (int j = 0; j < 4; j++) {
             uint32_t v = 0;
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-              const uint32_t idx = 16 * k + 4 * j + q;
-              if (idx < cnt) v |= rd.next(s_T, h.len_lo, h.len_hi) << (8 * q);
-            }
+            for (int q = 0; q < 4; q++)
+              if (16 * k + 4 * j + q < (int)cnt) v |= d.round1(s_T, len_lo, len_hi) << (8 * q);
             w[j] = v;
           }
-          s_rows[lane * 8 + (k ^ (lane & 7))] = make_uint4(w[0], w[1], w[2], w[3]);
+          s_tile[lane * 2 + (k ^ ((lane >> 2) & 1))] = make_uint4(w[0], w[1], w[2], w[3]);
         }
       }
       __syncwarp();
+      // the tile's row r is lane r's 32 output bytes: two 16-byte pieces per row
 #pragma unroll
-      for (int t = 0; t < 8; t++) {
-        const int r = 4 * t + (lane >> 3), q = lane & 7;
+      for (int t = 0; t < 2; t++) {
+        const int r = 16 * t + (lane >> 1), q = lane & 1;
         const uint64_t rc = g * kGroupChunks + r;
         const uint32_t rn = rc < h.n_chunks ? (uint32_t)min((uint64_t)cs, h.n - rc * cs) : 0u;
         const uint32_t off = i0 + 16 * q;
         if (off < rn) {
-          const uint4 val = s_rows[r * 8 + (q ^ (r & 7))];
+          const uint4* src = &s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
           uint8_t* dst = out + rc * cs + off;
           if (off + 16 <= rn) {
-            *reinterpret_cast<uint4*>(dst) = val;
+            *reinterpret_cast<uint4*>(dst) = *src;
           } else {
-            const uint8_t* src = reinterpret_cast<const uint8_t*>(&s_rows[r * 8 + (q ^ (r & 7))]);
-            for (uint32_t b = 0; b < rn - off; b++) dst[b] = src[b];
+            const uint8_t* sb = reinterpret_cast<const uint8_t*>(src);
+            for (uint32_t b = 0; b < rn - off; b++) dst[b] = sb[b];
           }
         }
       }
       __syncwarp();
     }
+    cp_async_wait<0>();
     if (exists) {
-      const uint64_t consumed = (uint64_t)rd.shifted * 32 + rd.o - (S & 31);
+      // bits taken into the buffer minus bits still in it = bits consumed
+      const uint64_t consumed = (uint64_t)(d.rpb / 4 - (S >> 5)) * 32 - (d.nb1 + 1) - (S & 31u);
       if (consumed != bits) set_status(status, QLC_ERR_CORRUPT);
     }
   }

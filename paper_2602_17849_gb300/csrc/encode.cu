@@ -4,8 +4,8 @@
 //   pass 1  each warp sums the code lengths of its chunks -> chunk_bits;
 //   look-back  the group publishes its padded byte size and finds the sum of
 //           all earlier groups' sizes (decoupled look-back, bounded waits);
-//   pass 2  the group's symbols are re-read (from L2: at most two groups per
-//           SM are in flight) and packed, 4096 symbols per tile: block scan of
+//   pass 2  the group's symbols are re-read (from L2: at most three groups
+//           per SM are in flight) and packed, 4096 symbols per tile: block scan of
 //           per-thread bit counts, MSB-first packing of each thread's 16
 //           codewords into a shared staging window, coalesced 16-byte stores
 //           of every completed 16-byte block.
@@ -16,8 +16,9 @@ namespace qlc {
 
 constexpr int kEncThreads = 256;
 constexpr int kEncWarps = kEncThreads / 32;
+constexpr int kEncCtasPerSm = 3;
 constexpr int kTile = kEncThreads * 16;
-constexpr int kStageWords = 4 + (kTile * kMaxCode + 31) / 32 + 4;
+constexpr int kStageWords = 4 + 4 + (kTile * kMaxCode + 31) / 32 + 4;
 constexpr int kPass1Unroll = 8;
 
 constexpr unsigned long long kFlagAgg = 1ull << 62;
@@ -27,6 +28,31 @@ constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per look-back wait
 
 __device__ __forceinline__ uint32_t fold(uint32_t b) { return b + (b >> 7); }
+
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+// 0x80000000 >> s with PTX semantics (0 for s >= 32).
+__device__ __forceinline__ uint32_t top_bit_shr(uint32_t s) {
+  uint32_t d;
+  asm("shr.b32 %0, %1, %2;" : "=r"(d) : "r"(0x80000000u), "r"(s));
+  return d;
+}
+
+// OR v into a shared word when p holds; predicated, so no branch.
+__device__ __forceinline__ void red_or_if(uint32_t saddr, uint32_t v, bool p) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.or.b32 [%0], %1;\n\t}" ::"r"(saddr),
+      "r"(v), "r"((uint32_t)p)
+      : "memory");
+}
 
 __device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
 #pragma unroll
@@ -39,13 +65,15 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
   return v;
 }
 
-__device__ __forceinline__ uint32_t len16(const uint32_t* s_len, uint4 q) {
+// Sum of the code lengths of 16 symbols (s_len: one byte per symbol).
+__device__ __forceinline__ uint32_t len16(const uint8_t* s_len, uint4 q) {
   const uint32_t w[4] = {q.x, q.y, q.z, q.w};
   uint32_t s = 0;
 #pragma unroll
   for (int k = 0; k < 4; k++)
 #pragma unroll
-    for (int j = 0; j < 4; j++) s += s_len[fold((w[k] >> (8 * j)) & 0xFFu)];
+    for (int j = 0; j < 4; j += 2)
+      s += s_len[__byte_perm(w[k], 0, 0x4440 + j)] + s_len[__byte_perm(w[k], 0, 0x4441 + j)];
   return s;
 }
 
@@ -115,14 +143,14 @@ __device__ void write_header(uint8_t* out, uint64_t n, uint32_t cs, uint64_t n_c
   if (idx_end + tid < P) out[idx_end + tid] = 0;
 }
 
-__global__ void __launch_bounds__(kEncThreads, 2)
+__global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm)
 encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restrict__ lut,
               uint32_t cs, uint8_t* __restrict__ out, unsigned int* __restrict__ ticket,
               unsigned long long* __restrict__ gstat, unsigned long long* __restrict__ out_bytes,
               uint32_t* __restrict__ status) {
   __shared__ uint32_t s_enc[257];  // MSB-aligned codeword | length, index fold(symbol)
-  __shared__ uint32_t s_len[257];
-  __shared__ uint32_t s_stage[kStageWords];
+  __shared__ uint8_t s_len[256];
+  __shared__ __align__(16) uint32_t s_stage[2][kStageWords];  // ping-pong, 4 guard words in front
   __shared__ uint32_t s_chunk_bits[kGroupChunks];
   __shared__ uint32_t s_warp[kEncWarps];
   __shared__ unsigned long long s_group;
@@ -142,9 +170,9 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
       return;
     }
     s_enc[fold(tid)] = (code << (32 - len)) | len;
-    s_len[fold(tid)] = len;
+    s_len[tid] = (uint8_t)len;
   }
-  for (int i = tid; i < kStageWords; i += kEncThreads) s_stage[i] = 0;
+  for (int i = tid; i < 2 * kStageWords; i += kEncThreads) (&s_stage[0][0])[i] = 0;
 
   const uint64_t n_chunks = (n + cs - 1) / cs;
   const uint64_t n_groups = n_groups_of(n_chunks);
@@ -153,6 +181,7 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
   unsigned long long* group_off = reinterpret_cast<unsigned long long*>(out + kIndexOff);
   uint16_t* chunk_bits = reinterpret_cast<uint16_t*>(out + kIndexOff + 8 * n_groups);
   const uint64_t group_syms = (uint64_t)kGroupChunks * cs;
+  const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(&s_stage[0][0]);
 
   while (true) {
     __syncthreads();
@@ -181,7 +210,7 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
           for (int u = 0; u < kPass1Unroll; u++) bits += len16(s_len, q[u]);
         }
         for (; k < nv; k += 32) bits += len16(s_len, ldg_nc_v4(v + k));
-        for (uint32_t t = nv * 16 + lane; t < m; t += 32) bits += s_len[fold(in[cbeg + t])];
+        for (uint32_t t = nv * 16 + lane; t < m; t += 32) bits += s_len[in[cbeg + t]];
         bits = warp_sum_u32(bits);
         if (lane == 0) chunk_bits[g * kGroupChunks + c] = (uint16_t)bits;
       }
@@ -213,9 +242,13 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
     if (s_err) continue;
     uint4* dst = reinterpret_cast<uint4*>(payload + s_excl);
 
-    // ---- pass 2: pack the group's codewords, tile by tile
+    // ---- pass 2: pack the group's codewords, tile by tile.  Two staging
+    // buffers alternate between tiles: a tile packs into one while the
+    // completed 16-byte blocks of the previous tile leave from the other, so
+    // each tile needs two barriers.
     uint32_t base_bit = 0;  // group-relative bit position of the tile start
-    uint32_t win = 0;       // group-relative word index of s_stage[0] (multiple of 4)
+    uint32_t win = 0;       // group-relative word index of stage word 4 (multiple of 4)
+    int cur = 0;            // staging buffer of this tile
     uint4 qn = make_uint4(0, 0, 0, 0);
     {
       const uint64_t my = gbeg + (uint64_t)tid * 16;
@@ -235,14 +268,19 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
         const uint64_t nx = my + kTile;
         if (nx + 16 <= gend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + nx));
       }
-      uint32_t e[16];
+      // 16 codewords -> 8 pairs: MSB-aligned (at most 22 bits), lengths in P/L.
+      // An entry is codeword << (32 - len) | len, so e & 31 == len.
+      uint32_t P[8], L8[8];
       uint32_t L = 0;
       const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int j = 0; j < 16; j++) {
-        const uint32_t ent = s_enc[fold((qw[j >> 2] >> (8 * (j & 3))) & 0xFFu)];
-        e[j] = j < cnt ? ent : 0u;
-        L += e[j] & 15u;
+      for (int k = 0; k < 8; k++) {
+        const int j0 = 2 * k, j1 = 2 * k + 1;
+        const uint32_t e0 = j0 < cnt ? s_enc[fold(__byte_perm(qw[j0 >> 2], 0, 0x4440 + (j0 & 3)))] : 0u;
+        const uint32_t e1 = j1 < cnt ? s_enc[fold(__byte_perm(qw[j1 >> 2], 0, 0x4440 + (j1 & 3)))] : 0u;
+        P[k] = (e0 & ~31u) | __funnelshift_r(e1 & ~31u, 0u, e0);  // second code right after the first
+        L8[k] = (e0 + e1) & 31u;  // the two lengths; code bits sit above bit 20
+        L += L8[k];
       }
       // block exclusive scan of L
       uint32_t incl = L;
@@ -261,46 +299,59 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
         total += t;
       }
       const uint32_t pos = base_bit + wpre + incl - L;
-      if (L) {
-        uint32_t wi = (pos >> 5) - win;
-        uint32_t nacc = pos & 31u;
-        unsigned long long acc = 0;
+      // Append the pairs to a 64-bit MSB-first accumulator (ahi:alo) in which
+      // the first f bits (1 <= f <= 32) of ahi are taken, g = f - 1.  A pair
+      // is placed with two multiply-adds by 2^(32 - f); each completed word is
+      // OR-ed into the staging buffer under a predicate (no branch).  A
+      // thread's first and last words can be shared with its neighbours.
+      {
+        const uint32_t r = pos & 31u;
+        uint32_t g = r ? r - 1 : 31u;
+        uint32_t wa = stage_s + (cur * kStageWords + 4 + (pos >> 5) - win - (r ? 0u : 1u)) * 4;
+        uint32_t ahi = 0, alo = 0;
 #pragma unroll
-        for (int j = 0; j < 16; j++) {
-          acc |= ((unsigned long long)(e[j] & ~15u) << 32) >> nacc;
-          nacc += e[j] & 15u;
-          if (nacc >= 32) {
-            atomicOr(&s_stage[wi++], (uint32_t)(acc >> 32));
-            acc <<= 32;
-            nacc -= 32;
-          }
+        for (int k = 0; k < 8; k++) {
+          const uint32_t qq = top_bit_shr(g);
+          ahi = mad_hi(P[k], qq, ahi);
+          alo = mad_lo(P[k], qq, alo);
+          g += L8[k];
+          const bool full = g >= 32;
+          red_or_if(wa, ahi, full && ahi != 0);
+          ahi = full ? alo : ahi;
+          alo = full ? 0u : alo;
+          g -= full ? 32u : 0u;
+          wa += full ? 4u : 0u;
         }
-        if (nacc) atomicOr(&s_stage[wi], (uint32_t)(acc >> 32));
+        red_or_if(wa, ahi, ahi != 0);
       }
       __syncthreads();
+      // completed 16-byte blocks go out; the partial last block moves to the
+      // other buffer; everything read here is zeroed for reuse
       const uint32_t end_bit = base_bit + total;
       const uint32_t nblk = ((end_bit >> 5) - win) / 4;
+      uint32_t* sb = &s_stage[cur][4];
       for (uint32_t b = tid; b < nblk; b += kEncThreads) {
-        const uint32_t* s = &s_stage[4 * b];
-        dst[win / 4 + b] = make_uint4(bswap32(s[0]), bswap32(s[1]), bswap32(s[2]), bswap32(s[3]));
+        uint4* s4 = reinterpret_cast<uint4*>(&sb[4 * b]);
+        const uint4 v = *s4;
+        dst[win / 4 + b] = make_uint4(bswap32(v.x), bswap32(v.y), bswap32(v.z), bswap32(v.w));
+        *s4 = make_uint4(0, 0, 0, 0);
       }
-      uint32_t carry = tid < 4 ? s_stage[4 * nblk + tid] : 0u;
-      __syncthreads();
-      const uint32_t used = 4 * nblk + 4;
-      for (uint32_t i = tid + 4; i < used; i += kEncThreads) s_stage[i] = 0;
-      if (tid < 4) s_stage[tid] = carry;
+      if (tid < 4) {
+        s_stage[cur ^ 1][4 + tid] = sb[4 * nblk + tid];
+        sb[4 * nblk + tid] = 0;
+      }
       win += 4 * nblk;
       base_bit = end_bit;
-      // (the next tile's first __syncthreads orders these writes)
+      cur ^= 1;
     }
     __syncthreads();
     // last, partial 16-byte block of the group (zero bits after the end)
-    if (tid == 0 && (base_bit & 127u)) {
-      const uint32_t* s = s_stage;
-      dst[win / 4] = make_uint4(bswap32(s[0]), bswap32(s[1]), bswap32(s[2]), bswap32(s[3]));
+    if (tid == 0) {
+      uint32_t* c = &s_stage[cur][4];
+      if (base_bit & 127u)
+        dst[win / 4] = make_uint4(bswap32(c[0]), bswap32(c[1]), bswap32(c[2]), bswap32(c[3]));
+      c[0] = c[1] = c[2] = c[3] = 0;
     }
-    __syncthreads();
-    if (tid < 4) s_stage[tid] = 0;
   }
 }
 
@@ -358,7 +409,7 @@ qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint3
   if (ws_bytes < ws_need) return QLC_ERR_CAPACITY;
   if (cudaMemsetAsync(d_ws, 0, ws_need, st) != cudaSuccess) return QLC_ERR_CUDA;
   const uint64_t n_groups = n_groups_of(n_chunks);
-  const uint64_t cap = (uint64_t)sm_count() * 2;
+  const uint64_t cap = (uint64_t)sm_count() * kEncCtasPerSm;
   const int grid = (int)(n_groups < cap ? n_groups : cap);
   unsigned int* ticket = static_cast<unsigned int*>(d_ws);
   unsigned long long* gstat =
