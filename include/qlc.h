@@ -147,6 +147,25 @@ qlc_status qlc_encode(const uint8_t *d_in, size_t n, const qlc_lut *d_lut,
                       void *d_ws, size_t ws_bytes, uint64_t *d_out_bytes,
                       uint32_t *d_status, qlc_stream_t stream);
 
+/* Same result as qlc_encode, for callers that cannot allocate device memory
+ * (for example a plugin whose host framework's allocator owns the GPU's
+ * memory, or a request path that must not call cudaMalloc).  The paper has no
+ * counterpart; this is a library convenience.  Instead of a caller workspace
+ * it uses scratch space built into the library: one array per GPU of
+ * 16 + 8 * 65536 bytes, held until the process exits, which bounds n to at
+ * most 65536 groups of 32 chunks (65536 * 32 * chunk_symbols symbols; e.g.
+ * 8 GiB at chunk 4096); larger n returns QLC_ERR_CAPACITY.  The first call on
+ * each device looks up that device's array address (with the device
+ * current), so make the first call on a device before any stream capture.
+ * All calls share the one array and each call clears it on `stream` before
+ * use: calls that may run at the same time on the GPU (different streams
+ * without ordering between them) race and must not be issued.  Other
+ * arguments, errors and alignment rules as for qlc_encode. */
+qlc_status qlc_encode_noalloc(const uint8_t *d_in, size_t n, const qlc_lut *d_lut,
+                              uint32_t chunk_symbols, uint8_t *d_out, size_t out_cap,
+                              uint64_t *d_out_bytes, uint32_t *d_status,
+                              qlc_stream_t stream);
+
 /* Decodes a container (Section 7).  d_in: in_bytes of container, 16-byte
  * aligned.  d_out: out_cap bytes, 16-byte aligned; the decoder writes
  * n = the header's symbol count bytes.  *d_n_out receives n.  The container

@@ -421,3 +421,54 @@ qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Encoding without any device allocation by the caller or the library.
+//
+// Some callers cannot allocate device memory: a plugin running inside a host
+// framework whose allocator owns all of the GPU's memory, or a request path
+// that must not call cudaMalloc (which can synchronise the device).  For them
+// the look-back state that qlc_encode keeps in a caller-provided workspace
+// lives instead in this file-scope device array, sized for up to
+// kNoAllocMaxGroups groups of 32 chunks.  Every GPU that loads the library
+// holds these bytes until the process exits.
+namespace qlc {
+constexpr uint64_t kNoAllocMaxGroups = 65536;
+constexpr size_t kNoAllocScratchBytes = 16 + 8 * kNoAllocMaxGroups;  // 512 KiB + 16 B
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current (the host-side symbol is not a device address).
+static void* noalloc_scratch_ptr(qlc_status* err) {
+  static void* cached[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *err = QLC_ERR_CUDA;
+    return nullptr;
+  }
+  if (!cached[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      *err = QLC_ERR_CUDA;
+      return nullptr;
+    }
+    cached[dev] = p;
+  }
+  return cached[dev];
+}
+}  // namespace qlc
+
+extern "C" qlc_status qlc_encode_noalloc(const uint8_t* d_in, size_t n, const qlc_lut* d_lut,
+                                          uint32_t chunk_symbols, uint8_t* d_out, size_t out_cap,
+                                          uint64_t* d_out_bytes, uint32_t* d_status,
+                                          qlc_stream_t stream) {
+  if (!chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
+  const uint64_t n_chunks = (n + chunk_symbols - 1) / chunk_symbols;
+  if (n_groups_of(n_chunks) > kNoAllocMaxGroups) return QLC_ERR_CAPACITY;
+  qlc_status err = QLC_OK;
+  void* ws = noalloc_scratch_ptr(&err);
+  if (!ws) return err;
+  // qlc_encode clears the part of the array it uses before its kernel runs.
+  return qlc_encode(d_in, n, d_lut, chunk_symbols, d_out, out_cap, ws, kNoAllocScratchBytes,
+                    d_out_bytes, d_status, stream);
+}
