@@ -177,6 +177,58 @@ qlc_status qlc_decode(const uint8_t *d_in, size_t in_bytes, uint8_t *d_out,
                       size_t out_cap, uint64_t *d_n_out, uint32_t *d_status,
                       qlc_stream_t stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many tensors ("shards", e.g. the 18 layers x 64 devices = 1152 shards per
+ * tensor type of Section 3) in one launch per step.  A batch is an array of
+ * descriptors in device memory.  Work is split into items of one group of 32
+ * chunks; persistent CTAs take items from a device-side counter, so shards of
+ * very different sizes share the GPU evenly.  Per-shard errors go to
+ * *d_status; other shards are unaffected. */
+typedef struct qlc_desc {
+  const void *in;      /* encode / histogram: the shard's symbols; decode: its container */
+  uint64_t in_bytes;   /* encode / histogram: n symbols; decode: container bytes */
+  void *out;           /* encode: container buffer; decode: decoded symbols */
+  uint64_t out_cap;    /* bytes available at out */
+  const qlc_lut *lut;  /* encode: this shard's LUT (shards may share one) */
+  uint64_t *out_bytes; /* encode: container size; decode: n (device pointer or NULL) */
+} qlc_desc;            /* 48 bytes */
+
+/* Launch shape knobs (an autotuner picks them); 0 = library default. */
+typedef struct qlc_launch {
+  uint16_t encode_ctas_per_sm; /* resident encode CTAs (256 threads) per SM, 1..3 */
+  uint16_t decode_ctas_per_sm; /* resident decode warps per SM, 1..26 */
+  uint32_t reserved;
+} qlc_launch;
+
+/* Device workspace for the batch calls below, for n_shards shards holding
+ * total_symbols symbols, encoded with chunk_symbols (decode batches of
+ * containers with that chunk size or larger also fit). */
+size_t qlc_batch_workspace_size(int n_shards, uint64_t total_symbols, uint32_t chunk_symbols);
+
+/* Histograms of the shards (Section 4).  shared = 0: d_hists holds
+ * n_shards x 256 counts, one histogram per shard; shared = 1: one histogram
+ * over all shards (an a-priori LUT per tensor type, Section 7).  Overwrites
+ * d_hists.  Uses d_ws.  Async on stream. */
+qlc_status qlc_histogram_batch(const qlc_desc *d_descs, int n_shards, uint64_t *d_hists, int shared,
+                               void *d_ws, size_t ws_bytes, qlc_stream_t stream);
+
+/* One LUT per histogram (Section 7), each with the scheme among
+ * h_schemes[0..n_schemes) that gives it the fewest payload bits (Section 6).
+ * d_hists: n_luts x 256; d_luts: n_luts qlc_lut.  Async on stream. */
+qlc_status qlc_build_lut_batch(const uint64_t *d_hists, int n_luts, const qlc_scheme *h_schemes,
+                               int n_schemes, qlc_lut *d_luts, qlc_stream_t stream);
+
+/* Encodes every shard into its container (as qlc_encode); desc.out_bytes
+ * receives each container's size.  Async on stream. */
+qlc_status qlc_encode_batch(const qlc_desc *d_descs, int n_shards, uint32_t chunk_symbols,
+                            void *d_ws, size_t ws_bytes, uint32_t *d_status,
+                            const qlc_launch *h_launch, qlc_stream_t stream);
+
+/* Decodes every shard's container (as qlc_decode); desc.out_bytes receives
+ * each n.  Async on stream. */
+qlc_status qlc_decode_batch(const qlc_desc *d_descs, int n_shards, void *d_ws, size_t ws_bytes,
+                            uint32_t *d_status, const qlc_launch *h_launch, qlc_stream_t stream);
+
 /* Reads n and the total container size from a host copy of the first
  * QLC_HEADER_BYTES bytes of a container (for sizing buffers).  Host only;
  * QLC_ERR_CORRUPT for a bad magic/version, QLC_ERR_ARG for NULL or

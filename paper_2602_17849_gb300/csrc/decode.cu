@@ -199,56 +199,40 @@ struct LaneDec {
   }
 };
 
-__global__ void __launch_bounds__(32, kDecCtasPerSm)
-decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __restrict__ out,
-              uint64_t out_cap, unsigned long long* __restrict__ n_out, uint32_t* __restrict__ status) {
-  __shared__ __align__(16) uint8_t s_T[2048];
-  __shared__ __align__(128) uint4 s_ring[32 * kRingVec];
-  __shared__ __align__(16) uint4 s_tile[32 * (kBlk / 16)];
-  __shared__ __align__(16) uint8_t s_dec[256];
-  __shared__ uint32_t s_seen[8];
-  const int lane = threadIdx.x;
+struct DecShared {
+  uint8_t T[2048];
+  __align__(128) uint4 ring[32 * kRingVec];
+  __align__(16) uint4 tile[32 * (kBlk / 16)];
+  __align__(16) uint8_t dec[256];
+  uint32_t seen[8];
+};
 
-  DecHeader h;
-  const uint32_t err = parse_header(in, in_bytes, out_cap, &h, s_seen, lane);
-  if (err) {
-    if (blockIdx.x == 0 && lane == 0) {
-      if (err == QLC_ERR_CAPACITY) *n_out = h.n;
-      set_status(status, err);
-    }
-    return;
-  }
-  if (blockIdx.x == 0 && lane == 0) *n_out = h.n;
-  if (blockIdx.x >= h.n_groups) return;
-
-  // code -> symbol table: every code (i << bits[i]) | s of every area i maps
-  // to dec[offset_i + s] (offset 0 for 8-bit areas); dec staged in shared.
-  reinterpret_cast<uint32_t*>(s_dec)[lane] = reinterpret_cast<const uint32_t*>(in + 64)[lane];
-  reinterpret_cast<uint32_t*>(s_dec)[lane + 32] = reinterpret_cast<const uint32_t*>(in + 64)[lane + 32];
+// code -> symbol table: every code (i << bits[i]) | s of every area i maps to
+// dec[offset_i + s] (offset 0 for 8-bit areas); dec is staged in shared.
+__device__ void build_table(const uint8_t* in, DecShared& sm, int lane) {
+  reinterpret_cast<uint32_t*>(sm.dec)[lane] = reinterpret_cast<const uint32_t*>(in + 64)[lane];
+  reinterpret_cast<uint32_t*>(sm.dec)[lane + 32] = reinterpret_cast<const uint32_t*>(in + 64)[lane + 32];
   __syncwarp();
-  {
-    uint32_t base = 0;
-    for (int i = 0; i < 8; i++) {
-      const uint32_t b = in[40 + i];
-      for (uint32_t s = lane; s < (1u << b); s += 32) s_T[(i << b) | s] = s_dec[b == 8 ? s : base + s];
-      base += *reinterpret_cast<const uint16_t*>(in + 24 + 2 * i);
-    }
+  uint32_t base = 0;
+  for (int i = 0; i < 8; i++) {
+    const uint32_t b = in[40 + i];
+    for (uint32_t s = lane; s < (1u << b); s += 32) sm.T[(i << b) | s] = sm.dec[b == 8 ? s : base + s];
+    base += *reinterpret_cast<const uint16_t*>(in + 24 + 2 * i);
   }
   __syncwarp();
+}
 
+// Decodes group g of a validated container (one warp; lane = chunk).
+__device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
+                             uint64_t g, DecShared& sm, LaneDec& d, uint32_t* status, int lane) {
   const unsigned long long* group_off = reinterpret_cast<const unsigned long long*>(in + kIndexOff);
   const uint16_t* chunk_bits = reinterpret_cast<const uint16_t*>(in + kIndexOff + 8 * h.n_groups);
   const uint4* vbase = reinterpret_cast<const uint4*>(in + h.P);
   const uint32_t cs = h.cs;
   const uint32_t len_lo = h.len_lo, len_hi = h.len_hi;
-  LaneDec d;
-  d.ring_s = (uint32_t)__cvta_generic_to_shared(&s_ring[lane * kRingVec]);
-  if (__cvta_generic_to_shared(s_ring) & 127u) {  // the ring addressing relies on it
-    if (lane == 0) set_status(status, QLC_ERR_CUDA);
-    return;
-  }
-
-  for (uint64_t g = blockIdx.x; g < h.n_groups; g += gridDim.x) {
+  const uint8_t* s_T = sm.T;
+  uint4* s_tile = sm.tile;
+  do {
     const uint64_t c = g * kGroupChunks + lane;
     const bool exists = c < h.n_chunks;
     const uint32_t nsym = exists ? (uint32_t)min((uint64_t)cs, h.n - c * cs) : 0u;
@@ -266,7 +250,7 @@ decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __rest
                           gnext <= h.payload_bytes && gnext - goff == align16((gbits + 7u) / 8u);
     if (!group_ok) {
       if (lane == 0) set_status(status, QLC_ERR_CORRUPT);
-      continue;
+      break;
     }
     // lane start bit (group-relative), ring fill, buffer fill
     const uint32_t S = incl - bits;
@@ -345,6 +329,88 @@ decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __rest
       const uint64_t consumed = (uint64_t)(d.rpb / 4 - (S >> 5)) * 32 - (d.nb1 + 1) - (S & 31u);
       if (consumed != bits) set_status(status, QLC_ERR_CORRUPT);
     }
+  } while (false);
+}
+
+// One container: every CTA (one warp) validates the header, builds its table
+// and decodes groups blockIdx.x, blockIdx.x + gridDim.x, ...
+__global__ void __launch_bounds__(32, kDecCtasPerSm)
+decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __restrict__ out,
+              uint64_t out_cap, unsigned long long* __restrict__ n_out, uint32_t* __restrict__ status) {
+  __shared__ DecShared sm;
+  const int lane = threadIdx.x;
+  DecHeader h;
+  const uint32_t err = parse_header(in, in_bytes, out_cap, &h, sm.seen, lane);
+  if (err) {
+    if (blockIdx.x == 0 && lane == 0) {
+      if (err == QLC_ERR_CAPACITY) *n_out = h.n;
+      set_status(status, err);
+    }
+    return;
+  }
+  if (blockIdx.x == 0 && lane == 0) *n_out = h.n;
+  if (blockIdx.x >= h.n_groups) return;
+  if (__cvta_generic_to_shared(sm.ring) & 127u) {  // the ring addressing relies on it
+    if (lane == 0) set_status(status, QLC_ERR_CUDA);
+    return;
+  }
+  build_table(in, sm, lane);
+  LaneDec d;
+  d.ring_s = (uint32_t)__cvta_generic_to_shared(&sm.ring[lane * kRingVec]);
+  for (uint64_t g = blockIdx.x; g < h.n_groups; g += gridDim.x) decode_group(h, in, out, g, sm, d, status, lane);
+}
+
+// A batch: warps take (shard, group) items from a device counter; a warp
+// re-reads the header and rebuilds its table when its shard changes.
+__global__ void __launch_bounds__(32, kDecCtasPerSm)
+decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
+                    const unsigned long long* __restrict__ item_base, unsigned int* __restrict__ ticket,
+                    uint32_t* __restrict__ status) {
+  __shared__ DecShared sm;
+  const int lane = threadIdx.x;
+  if (__cvta_generic_to_shared(sm.ring) & 127u) {
+    if (lane == 0) set_status(status, QLC_ERR_CUDA);
+    return;
+  }
+  const unsigned long long total = item_base[n_shards];
+  LaneDec d;
+  d.ring_s = (uint32_t)__cvta_generic_to_shared(&sm.ring[lane * kRingVec]);
+  int cur = -1, bad = -1;
+  DecHeader h;
+  while (true) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(ticket, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= total) break;
+    int sh = 0;
+    {
+      int lo = 0, hi = n_shards - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (item_base[mid] <= t) lo = mid; else hi = mid - 1;
+      }
+      sh = lo;
+    }
+    if (sh == bad) continue;
+    const qlc_desc dd = descs[sh];
+    const uint8_t* in = static_cast<const uint8_t*>(dd.in);
+    const uint64_t g = t - item_base[sh];
+    if (sh != cur) {
+      const uint32_t err = parse_header(in, dd.in_bytes, dd.out_cap, &h, sm.seen, lane);
+      if (err) {
+        if (lane == 0) {
+          if (err == QLC_ERR_CAPACITY && dd.out_bytes) *dd.out_bytes = h.n;
+          set_status(status, err);
+        }
+        bad = sh;
+        cur = -1;
+        continue;
+      }
+      build_table(in, sm, lane);
+      cur = sh;
+    }
+    if (g == 0 && lane == 0 && dd.out_bytes) *dd.out_bytes = h.n;
+    if (g < h.n_groups) decode_group(h, in, static_cast<uint8_t*>(dd.out), g, sm, d, status, lane);
   }
 }
 
@@ -362,5 +428,21 @@ extern "C" qlc_status qlc_decode(const uint8_t* d_in, size_t in_bytes, uint8_t* 
   const int grid = (int)(max_groups < 1 ? 1 : (max_groups < cap ? max_groups : cap));
   decode_kernel<<<grid, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       d_in, in_bytes, d_out, out_cap, reinterpret_cast<unsigned long long*>(d_n_out), d_status);
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+extern "C" qlc_status qlc_decode_batch(const qlc_desc* d_descs, int n_shards, void* d_ws, size_t ws_bytes,
+                                       uint32_t* d_status, const qlc_launch* h_launch, qlc_stream_t stream) {
+  if (!d_descs || n_shards < 1 || !d_ws) return QLC_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_ws) & 15u) != 0) return QLC_ERR_ARG;
+  BatchWs w;
+  if (!batch_ws_layout(d_ws, ws_bytes, n_shards, &w)) return QLC_ERR_CAPACITY;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  plan_kernel<<<1, kPlanThreads, 0, st>>>(kPlanDecode, d_descs, n_shards, 0, w, d_status);
+  if (cudaGetLastError() != cudaSuccess) return QLC_ERR_CUDA;
+  int per_sm = kDecCtasPerSm;
+  if (h_launch && h_launch->decode_ctas_per_sm > 0 && h_launch->decode_ctas_per_sm < kDecCtasPerSm)
+    per_sm = h_launch->decode_ctas_per_sm;
+  decode_batch_kernel<<<sm_count() * per_sm, 32, 0, st>>>(d_descs, n_shards, w.item_base, w.ticket, d_status);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }

@@ -27,8 +27,6 @@ constexpr unsigned long long kFlagError = 3ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per look-back wait
 
-__device__ __forceinline__ uint32_t fold(uint32_t b) { return b + (b >> 7); }
-
 __device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
   asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
@@ -44,6 +42,13 @@ __device__ __forceinline__ uint32_t top_bit_shr(uint32_t s) {
   uint32_t d;
   asm("shr.b32 %0, %1, %2;" : "=r"(d) : "r"(0x80000000u), "r"(s));
   return d;
+}
+
+// Streaming (evict-first) 16-byte store: the container is written once and
+// should not push the input, which pass 2 re-reads, out of L2.
+__device__ __forceinline__ void st_cs_v4(uint4* p, uint4 v) {
+  asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
 }
 
 // OR v into a shared word when p holds; predicated, so no branch.
@@ -81,11 +86,11 @@ __device__ __forceinline__ uint32_t len16(const uint8_t* s_len, uint4 q) {
 // returns the byte offset of the group (sum of all earlier groups' sizes).
 // Every wait is bounded; on timeout *err is set and an error flag is
 // published so that later groups stop waiting too.
-__device__ unsigned long long lookback(unsigned long long* gstat, uint64_t g, uint64_t gbytes,
-                                       int lane, bool* err) {
+__device__ unsigned long long lookback(unsigned long long* gstat, uint64_t g, uint64_t first,
+                                       uint64_t gbytes, int lane, bool* err) {
   *err = false;
-  if (g == 0) {
-    if (lane == 0) st_release_u64(&gstat[0], kFlagPrefix | gbytes);
+  if (g == first) {
+    if (lane == 0) st_release_u64(&gstat[g], kFlagPrefix | gbytes);
     return 0;
   }
   if (lane == 0) st_release_u64(&gstat[g], kFlagAgg | gbytes);
@@ -93,8 +98,8 @@ __device__ unsigned long long lookback(unsigned long long* gstat, uint64_t g, ui
   int64_t idx = (int64_t)g - 1 - lane;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
-    unsigned long long v = kFlagPrefix;  // lanes before group 0 (never reached)
-    if (idx >= 0) {
+    unsigned long long v = kFlagPrefix;  // before the shard's first group: prefix 0
+    if (idx >= (int64_t)first) {
       while (true) {
         v = ld_acquire_u64(&gstat[idx]);
         if (v >> 62) break;
@@ -143,52 +148,126 @@ __device__ void write_header(uint8_t* out, uint64_t n, uint32_t cs, uint64_t n_c
   if (idx_end + tid < P) out[idx_end + tid] = 0;
 }
 
+// Work source of the encode kernel: one tensor (descs == nullptr), or the
+// shards of a batch, whose groups are numbered consecutively shard after
+// shard (item_base[s] = first item of shard s, item_base[n_shards] = total).
+struct EncArgs {
+  const uint8_t* in;
+  uint64_t n;
+  const qlc_lut* lut;
+  uint8_t* out;
+  unsigned long long* out_bytes;
+  uint64_t n_items;  // one tensor: its groups
+  const qlc_desc* descs;
+  const unsigned long long* item_base;
+  int n_shards;
+  uint32_t cs;
+  unsigned int* ticket;
+  unsigned long long* gstat;
+  uint32_t* status;
+};
+
+// Largest s with item_base[s] <= t (the shard holding item t).
+__device__ __forceinline__ int shard_of(const unsigned long long* item_base, int n_shards,
+                                        unsigned long long t) {
+  int lo = 0, hi = n_shards - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (item_base[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm)
-encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restrict__ lut,
-              uint32_t cs, uint8_t* __restrict__ out, unsigned int* __restrict__ ticket,
-              unsigned long long* __restrict__ gstat, unsigned long long* __restrict__ out_bytes,
-              uint32_t* __restrict__ status) {
-  __shared__ uint32_t s_enc[257];  // MSB-aligned codeword | length, index fold(symbol)
+encode_kernel(EncArgs A) {
+  __shared__ uint32_t s_enc[256];  // MSB-aligned codeword | length, by symbol
   __shared__ uint8_t s_len[256];
   __shared__ __align__(16) uint32_t s_stage[2][kStageWords];  // ping-pong, 4 guard words in front
   __shared__ uint32_t s_chunk_bits[kGroupChunks];
   __shared__ uint32_t s_warp[kEncWarps];
-  __shared__ unsigned long long s_group;
-  __shared__ unsigned long long s_excl;
+  __shared__ unsigned long long s_item, s_first, s_excl;
+  __shared__ const uint8_t* s_in;
+  __shared__ uint64_t s_n;
+  __shared__ const qlc_lut* s_lut;
+  __shared__ uint8_t* s_out;
+  __shared__ unsigned long long* s_ob;
   __shared__ int s_err;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  {
-    // A LUT entry must be a codeword of 3..11 bits; anything else (a LUT not
-    // made by qlc_build_lut*) would overrun the staging window and the
-    // output bound, so the kernel refuses it.
-    const uint32_t e = lut->enc[tid];
-    const uint32_t len = e & 15u, code = e >> 4;
-    const bool bad = len < 3 || len > kMaxCode || (code >> len) != 0;
-    if (__syncthreads_or(bad)) {
-      if (blockIdx.x == 0 && tid == 0) set_status(status, QLC_ERR_ARG);
-      return;
-    }
-    s_enc[fold(tid)] = (code << (32 - len)) | len;
-    s_len[tid] = (uint8_t)len;
-  }
-  for (int i = tid; i < 2 * kStageWords; i += kEncThreads) (&s_stage[0][0])[i] = 0;
-
-  const uint64_t n_chunks = (n + cs - 1) / cs;
-  const uint64_t n_groups = n_groups_of(n_chunks);
-  const uint64_t P = payload_start(n_chunks);
-  uint8_t* payload = out + P;
-  unsigned long long* group_off = reinterpret_cast<unsigned long long*>(out + kIndexOff);
-  uint16_t* chunk_bits = reinterpret_cast<uint16_t*>(out + kIndexOff + 8 * n_groups);
+  const uint32_t cs = A.cs;
   const uint64_t group_syms = (uint64_t)kGroupChunks * cs;
   const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(&s_stage[0][0]);
+  const uint64_t n_items = A.descs ? A.item_base[A.n_shards] : A.n_items;
+  const qlc_lut* cur_lut = nullptr;
+  for (int i = tid; i < 2 * kStageWords; i += kEncThreads) (&s_stage[0][0])[i] = 0;
 
   while (true) {
     __syncthreads();
-    if (tid == 0) s_group = atomicAdd(ticket, 1u);
+    if (tid == 0) {
+      const unsigned long long t = atomicAdd(A.ticket, 1u);
+      s_item = t;
+      if (t < n_items) {
+        if (A.descs) {
+          const int sh = shard_of(A.item_base, A.n_shards, t);
+          const qlc_desc d = A.descs[sh];
+          s_first = A.item_base[sh];
+          s_in = static_cast<const uint8_t*>(d.in);
+          s_n = d.in_bytes;
+          s_lut = d.lut;
+          s_out = static_cast<uint8_t*>(d.out);
+          s_ob = reinterpret_cast<unsigned long long*>(d.out_bytes);
+        } else {
+          s_first = 0;
+          s_in = A.in;
+          s_n = A.n;
+          s_lut = A.lut;
+          s_out = A.out;
+          s_ob = A.out_bytes;
+        }
+      }
+    }
     __syncthreads();
-    const uint64_t g = s_group;
-    if (g >= n_groups) break;
+    const unsigned long long item = s_item;
+    if (item >= n_items) break;
+    const uint64_t g = item - s_first;  // group within its tensor
+    const uint8_t* in = s_in;
+    const uint64_t n = s_n;
+    uint8_t* out = s_out;
+    const qlc_lut* lut = s_lut;
+    if (lut != cur_lut) {
+      // A LUT entry must be a codeword of 3..11 bits; anything else (a LUT
+      // not made by qlc_build_lut*) would overrun the staging window and the
+      // output bound, so the tensor is refused.
+      const uint32_t e = lut->enc[tid];
+      const uint32_t len = e & 15u, code = e >> 4;
+      const bool bad = len < 3 || len > kMaxCode || (code >> len) != 0;
+      if (__syncthreads_or(bad)) {
+        if (tid == 0) {
+          set_status(A.status, QLC_ERR_ARG);
+          st_release_u64(&A.gstat[item], kFlagError);
+        }
+        cur_lut = nullptr;
+        continue;
+      }
+      s_enc[tid] = (code << (32 - len)) | len;
+      s_len[tid] = (uint8_t)len;
+      cur_lut = lut;
+      __syncthreads();
+    }
+    const uint64_t n_chunks = (n + cs - 1) / cs;
+    const uint64_t n_groups = n_groups_of(n_chunks);
+    const uint64_t P = payload_start(n_chunks);
+    if (n == 0) {  // an empty shard of a batch: header-only container
+      write_header(out, 0, cs, 0, lut, tid);
+      if (tid == 0) {
+        *reinterpret_cast<unsigned long long*>(out + 48) = 0;
+        if (s_ob) *s_ob = P;
+      }
+      continue;
+    }
+    uint8_t* payload = out + P;
+    unsigned long long* group_off = reinterpret_cast<unsigned long long*>(out + kIndexOff);
+    uint16_t* chunk_bits = reinterpret_cast<uint16_t*>(out + kIndexOff + 8 * n_groups);
     const uint64_t gbeg = g * group_syms;
     const uint64_t gend = min(gbeg + group_syms, n);
     if (g == 0) write_header(out, n, cs, n_chunks, lut, tid);
@@ -223,17 +302,17 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
       const uint32_t gbits = warp_sum_u32(s_chunk_bits[lane]);
       const uint64_t gbytes = align16((gbits + 7) / 8);
       bool err = false;
-      const unsigned long long excl = lookback(gstat, g, gbytes, lane, &err);
+      const unsigned long long excl = lookback(A.gstat, item, s_first, gbytes, lane, &err);
       if (lane == 0) {
         s_excl = excl;
         s_err = err;
         if (err) {
-          set_status(status, QLC_ERR_TIMEOUT);
+          set_status(A.status, QLC_ERR_TIMEOUT);
         } else {
           group_off[g] = excl;
           if (g == n_groups - 1) {
             *reinterpret_cast<unsigned long long*>(out + 48) = excl + gbytes;
-            *out_bytes = P + excl + gbytes;
+            if (s_ob) *s_ob = P + excl + gbytes;
           }
         }
       }
@@ -273,11 +352,17 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
       uint32_t P[8], L8[8];
       uint32_t L = 0;
       const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+      uint32_t e[16];
+      if (cnt == 16) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) e[j] = s_enc[__byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3))];
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; j++) e[j] = j < cnt ? s_enc[__byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3))] : 0u;
+      }
 #pragma unroll
       for (int k = 0; k < 8; k++) {
-        const int j0 = 2 * k, j1 = 2 * k + 1;
-        const uint32_t e0 = j0 < cnt ? s_enc[fold(__byte_perm(qw[j0 >> 2], 0, 0x4440 + (j0 & 3)))] : 0u;
-        const uint32_t e1 = j1 < cnt ? s_enc[fold(__byte_perm(qw[j1 >> 2], 0, 0x4440 + (j1 & 3)))] : 0u;
+        const uint32_t e0 = e[2 * k], e1 = e[2 * k + 1];
         P[k] = (e0 & ~31u) | __funnelshift_r(e1 & ~31u, 0u, e0);  // second code right after the first
         L8[k] = (e0 + e1) & 31u;  // the two lengths; code bits sit above bit 20
         L += L8[k];
@@ -333,7 +418,7 @@ encode_kernel(const uint8_t* __restrict__ in, uint64_t n, const qlc_lut* __restr
       for (uint32_t b = tid; b < nblk; b += kEncThreads) {
         uint4* s4 = reinterpret_cast<uint4*>(&sb[4 * b]);
         const uint4 v = *s4;
-        dst[win / 4 + b] = make_uint4(bswap32(v.x), bswap32(v.y), bswap32(v.z), bswap32(v.w));
+        st_cs_v4(&dst[win / 4 + b], make_uint4(bswap32(v.x), bswap32(v.y), bswap32(v.z), bswap32(v.w)));
         *s4 = make_uint4(0, 0, 0, 0);
       }
       if (tid < 4) {
@@ -389,6 +474,14 @@ size_t qlc_encode_workspace_size(size_t n, uint32_t chunk_symbols) {
   return (size_t)(16 + 8 * n_groups_of(n_chunks));
 }
 
+static int enc_grid(uint64_t items, const qlc_launch* launch) {
+  int per_sm = kEncCtasPerSm;
+  if (launch && launch->encode_ctas_per_sm > 0 && launch->encode_ctas_per_sm < kEncCtasPerSm)
+    per_sm = launch->encode_ctas_per_sm;
+  const uint64_t cap = (uint64_t)sm_count() * per_sm;
+  return (int)(items < 1 ? 1 : (items < cap ? items : cap));
+}
+
 qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint32_t chunk_symbols,
                       uint8_t* d_out, size_t out_cap, void* d_ws, size_t ws_bytes,
                       uint64_t* d_out_bytes, uint32_t* d_status, qlc_stream_t stream) {
@@ -408,15 +501,41 @@ qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint3
   const size_t ws_need = qlc_encode_workspace_size(n, chunk_symbols);
   if (ws_bytes < ws_need) return QLC_ERR_CAPACITY;
   if (cudaMemsetAsync(d_ws, 0, ws_need, st) != cudaSuccess) return QLC_ERR_CUDA;
-  const uint64_t n_groups = n_groups_of(n_chunks);
-  const uint64_t cap = (uint64_t)sm_count() * kEncCtasPerSm;
-  const int grid = (int)(n_groups < cap ? n_groups : cap);
-  unsigned int* ticket = static_cast<unsigned int*>(d_ws);
-  unsigned long long* gstat =
-      reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(d_ws) + 16);
-  encode_kernel<<<grid, kEncThreads, 0, st>>>(d_in, n, d_lut, chunk_symbols, d_out, ticket, gstat,
-                                              reinterpret_cast<unsigned long long*>(d_out_bytes),
-                                              d_status);
+  EncArgs A = {};
+  A.in = d_in;
+  A.n = n;
+  A.lut = d_lut;
+  A.out = d_out;
+  A.out_bytes = reinterpret_cast<unsigned long long*>(d_out_bytes);
+  A.n_items = n_groups_of(n_chunks);
+  A.cs = chunk_symbols;
+  A.ticket = static_cast<unsigned int*>(d_ws);
+  A.gstat = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(d_ws) + 16);
+  A.status = d_status;
+  encode_kernel<<<enc_grid(A.n_items, nullptr), kEncThreads, 0, st>>>(A);
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+qlc_status qlc_encode_batch(const qlc_desc* d_descs, int n_shards, uint32_t chunk_symbols, void* d_ws,
+                            size_t ws_bytes, uint32_t* d_status, const qlc_launch* h_launch,
+                            qlc_stream_t stream) {
+  if (!d_descs || n_shards < 1 || !d_ws || !chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
+  if ((reinterpret_cast<uintptr_t>(d_ws) & 15u) != 0) return QLC_ERR_ARG;
+  BatchWs w;
+  if (!batch_ws_layout(d_ws, ws_bytes, n_shards, &w)) return QLC_ERR_CAPACITY;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  plan_kernel<<<1, kPlanThreads, 0, st>>>(kPlanEncode, d_descs, n_shards, chunk_symbols, w, d_status);
+  if (cudaGetLastError() != cudaSuccess) return QLC_ERR_CUDA;
+  EncArgs A = {};
+  A.descs = d_descs;
+  A.item_base = w.item_base;
+  A.n_shards = n_shards;
+  A.cs = chunk_symbols;
+  A.ticket = w.ticket;
+  A.gstat = w.gstat;
+  A.status = d_status;
+  // the item count is only known on the device: launch the full resident grid
+  encode_kernel<<<enc_grid(~0ull, h_launch), kEncThreads, 0, st>>>(A);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
 

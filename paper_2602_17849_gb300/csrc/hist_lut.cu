@@ -107,10 +107,13 @@ struct SchemeSet {
 // Section 6: the scheme can be adapted to the distribution.  Each candidate
 // is scored by its payload bits sum_s count[s] * len(rank[s]) and the
 // smallest wins (ties: the earlier candidate).
+// One CTA per histogram: CTA b builds luts[b] from hists[b * 256 ...].
 __global__ void __launch_bounds__(256)
-lut_best_kernel(const unsigned long long* __restrict__ hist, SchemeSet set, qlc_lut* __restrict__ lut) {
+lut_best_kernel(const unsigned long long* __restrict__ hists, SchemeSet set, qlc_lut* __restrict__ luts) {
   __shared__ unsigned long long h[256];
   __shared__ unsigned long long bits[8][8];
+  const unsigned long long* hist = hists + (size_t)blockIdx.x * 256;
+  qlc_lut* lut = luts + blockIdx.x;
   const int s = threadIdx.x;
   h[s] = hist[s];
   __syncthreads();
@@ -234,6 +237,21 @@ qlc_status qlc_build_lut_best(const uint64_t* d_hist, const qlc_scheme* h_scheme
   }
   lut_best_kernel<<<1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const unsigned long long*>(d_hist), set, d_lut);
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+qlc_status qlc_build_lut_batch(const uint64_t* d_hists, int n_luts, const qlc_scheme* h_schemes,
+                               int n_schemes, qlc_lut* d_luts, qlc_stream_t stream) {
+  if (!d_hists || !d_luts || !h_schemes || n_luts < 1 || n_schemes < 1 || n_schemes > 8)
+    return QLC_ERR_ARG;
+  SchemeSet set;
+  set.count = n_schemes;
+  for (int k = 0; k < n_schemes; k++) {
+    if (!scheme_valid(&h_schemes[k])) return QLC_ERR_ARG;
+    set.s[k] = clean_scheme(&h_schemes[k]);
+  }
+  lut_best_kernel<<<n_luts, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      reinterpret_cast<const unsigned long long*>(d_hists), set, d_luts);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
 

@@ -76,4 +76,36 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
+// ----------------------------------------------------------------- batches
+// Batch workspace: 64 bytes of counters, item_base[n_shards + 1] (first work
+// item of each shard; the last entry is the total), then one look-back word
+// per encode work item.
+struct BatchWs {
+  unsigned int* ticket;                // shared by encode / decode / histogram
+  unsigned long long* item_base;
+  unsigned long long* gstat;
+  unsigned long long gstat_cap;        // look-back words available
+};
+inline bool batch_ws_layout(void* ws, size_t bytes, int n_shards, BatchWs* w) {
+  const size_t head = 64 + 8 * (size_t)(n_shards + 1);
+  if (bytes < head) return false;
+  uint8_t* p = static_cast<uint8_t*>(ws);
+  w->ticket = reinterpret_cast<unsigned int*>(p);
+  w->item_base = reinterpret_cast<unsigned long long*>(p + 64);
+  w->gstat = reinterpret_cast<unsigned long long*>(p + head);
+  w->gstat_cap = (bytes - head) / 8;
+  return true;
+}
+
+enum PlanKind { kPlanHistogram = 0, kPlanEncode = 1, kPlanDecode = 2 };
+constexpr int kPlanThreads = 1024;
+constexpr uint64_t kHistItem = 256 * 1024;  // symbols per histogram work item
+
+// One CTA: the number of work items of every shard (histogram: 256 KiB
+// pieces; encode: groups of 32 chunks; decode: the container's groups),
+// their exclusive prefix in item_base, and zeroed counters / look-back words.
+// Shards that cannot be processed get no items and set *status.
+__global__ void plan_kernel(int kind, const qlc_desc* descs, int n_shards, uint32_t cs, BatchWs w,
+                            uint32_t* status);
+
 }  // namespace qlc

@@ -150,3 +150,34 @@ def cfg3_shards(n_shards: int = 1152, lo: int = 64 << 10, hi: int = 16 << 20, ba
         kinds.append(cycle[i % 3])
         seeds.append(base_seed + i)
     return sizes, kinds, seeds
+
+
+def make_shards(sizes, kinds, seeds, device="cpu"):
+    """One arena with every shard at a 16-byte aligned offset; returns
+    (arena, list of shard views)."""
+    offs, o = [], 0
+    for n in sizes:
+        offs.append(o)
+        o += (n + 15) // 16 * 16
+    arena = torch.zeros(max(o, 16), dtype=torch.uint8, device=device)
+    views = []
+    for off, n, kind, seed in zip(offs, sizes, kinds, seeds):
+        v = arena[off:off + n]
+        if n:
+            v.copy_(make_e4m3(kind, n, seed, device=device))
+        views.append(v)
+    return arena, views
+
+
+def cfg3_batch(device="cpu", n_shards: int = 1152):
+    """The batched workload: 1152 shards, log-uniform 64 KiB - 16 MiB,
+    activations / weights / gradients (Student-t, Gaussian, Laplace)."""
+    sizes, kinds, seeds = cfg3_shards(n_shards)
+    return make_shards(sizes, kinds, seeds, device)
+
+
+def cfg4_batch(device="cpu", n_shards: int = 64, size: int = 64 << 20):
+    """Batched large: 64 shards x 64 MiB of Laplace(b=1) with 1% N(0, 20^2)
+    outliers, seeds 2000 + i."""
+    return make_shards([size] * n_shards, ["laplace_outliers"] * n_shards,
+                       [2000 + i for i in range(n_shards)], device)

@@ -37,7 +37,18 @@ class qlc_lut(ctypes.Structure):
     _fields_ = [("scheme", qlc_scheme), ("enc", ctypes.c_uint16 * 256), ("dec", ctypes.c_uint8 * 256)]
 
 
+class qlc_desc(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("in_bytes", ctypes.c_uint64), ("out", ctypes.c_void_p),
+                ("out_cap", ctypes.c_uint64), ("lut", ctypes.c_void_p), ("out_bytes", ctypes.c_void_p)]
+
+
+class qlc_launch(ctypes.Structure):
+    _fields_ = [("encode_ctas_per_sm", ctypes.c_uint16), ("decode_ctas_per_sm", ctypes.c_uint16),
+                ("reserved", ctypes.c_uint32)]
+
+
 assert ctypes.sizeof(qlc_scheme) == SCHEME_BYTES and ctypes.sizeof(qlc_lut) == LUT_BYTES
+assert ctypes.sizeof(qlc_desc) == 48 and ctypes.sizeof(qlc_launch) == 8
 
 
 def _load() -> ctypes.CDLL:
@@ -62,8 +73,17 @@ def _load() -> ctypes.CDLL:
     L.qlc_encode.argtypes = [P, sz, P, u32, P, sz, P, sz, P, P, P]
     L.qlc_decode.argtypes = [P, sz, P, sz, P, P, P]
     L.qlc_peek_header.argtypes = [P, sz, P, P]
+    u64 = ctypes.c_uint64
+    L.qlc_encode_noalloc.argtypes = [P, sz, P, u32, P, sz, P, P, P]
+    L.qlc_batch_workspace_size.argtypes = [i32, u64, u32]
+    L.qlc_batch_workspace_size.restype = sz
+    L.qlc_histogram_batch.argtypes = [P, i32, P, i32, P, sz, P]
+    L.qlc_build_lut_batch.argtypes = [P, i32, P, i32, P, P]
+    L.qlc_encode_batch.argtypes = [P, i32, u32, P, sz, P, P, P]
+    L.qlc_decode_batch.argtypes = [P, i32, P, sz, P, P, P]
     for f in ("qlc_scheme_table", "qlc_histogram", "qlc_build_lut", "qlc_build_lut_host",
-              "qlc_build_lut_best", "qlc_encode", "qlc_decode", "qlc_peek_header"):
+              "qlc_build_lut_best", "qlc_encode", "qlc_decode", "qlc_peek_header", "qlc_encode_noalloc",
+              "qlc_histogram_batch", "qlc_build_lut_batch", "qlc_encode_batch", "qlc_decode_batch"):
         getattr(L, f).restype = i32
     return L
 
@@ -201,6 +221,65 @@ def qlc_peek_header(hdr: bytes):
     return int(n.value), int(c.value)
 
 
+def qlc_encode_noalloc(d_in: torch.Tensor, d_lut: torch.Tensor, chunk_symbols: int, d_out: torch.Tensor,
+                       d_out_bytes: torch.Tensor, d_status: torch.Tensor, n: int | None = None,
+                       stream=None) -> None:
+    n = _nbytes(d_in) if n is None else n
+    _check(lib.qlc_encode_noalloc(_ptr(d_in), n, _ptr(d_lut), int(chunk_symbols), _ptr(d_out),
+                                  _nbytes(d_out), _ptr(d_out_bytes), _ptr(d_status), _stream(stream)),
+           "qlc_encode_noalloc")
+
+
+def qlc_batch_workspace_size(n_shards: int, total_symbols: int, chunk_symbols: int = 4096) -> int:
+    return int(lib.qlc_batch_workspace_size(int(n_shards), int(total_symbols), int(chunk_symbols)))
+
+
+def _launch(launch):
+    if launch is None:
+        return None
+    if isinstance(launch, qlc_launch):
+        return ctypes.byref(launch)
+    e, d = launch
+    return ctypes.byref(qlc_launch(int(e), int(d), 0))
+
+
+def qlc_histogram_batch(d_descs: torch.Tensor, n_shards: int, d_hists: torch.Tensor, shared: bool,
+                        d_ws: torch.Tensor, stream=None) -> None:
+    _check(lib.qlc_histogram_batch(_ptr(d_descs), int(n_shards), _ptr(d_hists), int(bool(shared)),
+                                   _ptr(d_ws), _nbytes(d_ws), _stream(stream)), "qlc_histogram_batch")
+
+
+def qlc_build_lut_batch(d_hists: torch.Tensor, n_luts: int, schemes, d_luts: torch.Tensor,
+                        stream=None) -> None:
+    schemes = schemes if isinstance(schemes, (list, tuple)) else [schemes]
+    arr = (qlc_scheme * len(schemes))(*[as_scheme(x) for x in schemes])
+    _check(lib.qlc_build_lut_batch(_ptr(d_hists), int(n_luts), arr, len(schemes), _ptr(d_luts),
+                                   _stream(stream)), "qlc_build_lut_batch")
+
+
+def qlc_encode_batch(d_descs: torch.Tensor, n_shards: int, chunk_symbols: int, d_ws: torch.Tensor,
+                     d_status: torch.Tensor, launch=None, stream=None) -> None:
+    _check(lib.qlc_encode_batch(_ptr(d_descs), int(n_shards), int(chunk_symbols), _ptr(d_ws), _nbytes(d_ws),
+                                _ptr(d_status), _launch(launch), _stream(stream)), "qlc_encode_batch")
+
+
+def qlc_decode_batch(d_descs: torch.Tensor, n_shards: int, d_ws: torch.Tensor, d_status: torch.Tensor,
+                     launch=None, stream=None) -> None:
+    _check(lib.qlc_decode_batch(_ptr(d_descs), int(n_shards), _ptr(d_ws), _nbytes(d_ws), _ptr(d_status),
+                                _launch(launch), _stream(stream)), "qlc_decode_batch")
+
+
+def descs_tensor(rows, device) -> torch.Tensor:
+    """Device array of qlc_desc from (in, in_bytes, out, out_cap, lut, out_bytes) tuples of ints."""
+    arr = (qlc_desc * len(rows))(*[qlc_desc(*[int(v) for v in r]) for r in rows])
+    host = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+    return host.to(device)
+
+
+def _align16(v: int) -> int:
+    return (v + 15) // 16 * 16
+
+
 # ------------------------------------------------------------ conveniences
 
 class Codec:
@@ -274,3 +353,97 @@ def decode(container: torch.Tensor) -> torch.Tensor:
     if st != OK:
         raise QlcError(st, "qlc_decode")
     return out[:n]
+
+
+class Batch:
+    """Many shards encoded / decoded with one launch per step (qlc_*_batch).
+
+    shards: CUDA uint8 tensors (16-byte aligned starts).  One LUT per shard,
+    or one shared LUT built from the histogram of all shards.  Containers and
+    decoded outputs live in two arenas allocated once; encode() / decode()
+    launch only library kernels and never synchronise; capture() records both
+    as CUDA graphs.
+    """
+
+    def __init__(self, shards, chunk_symbols: int = 4096, schemes=(1,), shared_lut: bool = False,
+                 launch=None, device=None):
+        self.device = torch.device(device) if device is not None else shards[0].device
+        self.shards = list(shards)
+        self.n = len(self.shards)
+        self.chunk_symbols = int(chunk_symbols)
+        self.schemes = list(schemes) if isinstance(schemes, (list, tuple)) else [schemes]
+        self.shared = bool(shared_lut)
+        self.launch = launch
+        self.sizes = [s.numel() for s in self.shards]
+        self.total = sum(self.sizes)
+        caps = [qlc_encoded_size(n, self.chunk_symbols) for n in self.sizes]
+        if min(caps) == 0:
+            raise QlcError(ERR_ARG, "chunk_symbols")
+        self.cap_off = [0]
+        for c in caps:
+            self.cap_off.append(self.cap_off[-1] + _align16(c))
+        self.out_off = [0]
+        for n in self.sizes:
+            self.out_off.append(self.out_off[-1] + _align16(max(n, 1)))
+        z = dict(device=self.device)
+        self.containers = torch.empty(self.cap_off[-1], dtype=torch.uint8, **z)
+        self.decoded = torch.empty(self.out_off[-1], dtype=torch.uint8, **z)
+        n_luts = 1 if self.shared else self.n
+        self.hists = torch.zeros(n_luts * 256, dtype=torch.int64, **z)
+        self.luts = torch.zeros(n_luts * LUT_BYTES, dtype=torch.uint8, **z)
+        self.c_bytes = torch.zeros(self.n, dtype=torch.int64, **z)
+        self.n_out = torch.zeros(self.n, dtype=torch.int64, **z)
+        self.status = torch.zeros(1, dtype=torch.int32, **z)
+        self.ws = torch.zeros(qlc_batch_workspace_size(self.n, self.total, self.chunk_symbols),
+                              dtype=torch.uint8, **z)
+        cb, lb = self.containers.data_ptr(), self.luts.data_ptr()
+        enc = []
+        for i, x in enumerate(self.shards):
+            lut = lb if self.shared else lb + i * LUT_BYTES
+            enc.append((x.data_ptr(), self.sizes[i], cb + self.cap_off[i], caps[i], lut,
+                        self.c_bytes.data_ptr() + 8 * i))
+        self.enc_descs = descs_tensor(enc, self.device)
+        db = self.decoded.data_ptr()
+        dec = [(cb + self.cap_off[i], caps[i], db + self.out_off[i], self.sizes[i], 0,
+                self.n_out.data_ptr() + 8 * i) for i in range(self.n)]
+        self.dec_descs = descs_tensor(dec, self.device)
+        self.graphs = {}
+
+    def container(self, i: int) -> torch.Tensor:
+        return self.containers[self.cap_off[i]:self.cap_off[i + 1]]
+
+    def output(self, i: int) -> torch.Tensor:
+        return self.decoded[self.out_off[i]:self.out_off[i] + self.sizes[i]]
+
+    def encode(self, stream=None, build_luts: bool = True) -> None:
+        if build_luts:
+            qlc_histogram_batch(self.enc_descs, self.n, self.hists, self.shared, self.ws, stream=stream)
+            qlc_build_lut_batch(self.hists, 1 if self.shared else self.n, self.schemes, self.luts, stream=stream)
+        qlc_encode_batch(self.enc_descs, self.n, self.chunk_symbols, self.ws, self.status, self.launch,
+                         stream=stream)
+
+    def decode(self, stream=None) -> None:
+        qlc_decode_batch(self.dec_descs, self.n, self.ws, self.status, self.launch, stream=stream)
+
+    def capture(self) -> None:
+        """Record encode() and decode() as CUDA graphs (replay with replay())."""
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):  # warm up outside the capture
+            self.encode(stream=s)
+            self.decode(stream=s)
+        torch.cuda.current_stream(self.device).wait_stream(s)
+        for name, fn in (("encode", self.encode), ("decode", self.decode)):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn(stream=torch.cuda.current_stream(self.device))
+            self.graphs[name] = g
+
+    def replay(self, name: str) -> None:
+        self.graphs[name].replay()
+
+    def check(self) -> None:
+        st = int(self.status.item())
+        if st != OK:
+            self.status.zero_()
+            raise QlcError(st, "batch")

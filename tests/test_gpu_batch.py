@@ -1,0 +1,184 @@
+"""Batched (persistent, many-shard) encode and decode against the oracle and
+against the single-tensor path: bit-exact containers and outputs, per-shard and
+shared LUTs, scheme selection, CUDA-graph replay, error isolation, and the
+full-size batched workloads on sampled shards."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2602_17849_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qlc():
+    assert torch.cuda.is_available()
+    from paper_2602_17849_gb300 import _build
+    _build.build()
+    from paper_2602_17849_gb300 import qlc as q
+    return q
+
+
+def _mixed(device="cuda"):
+    sizes = [0, 1, 17, 128, 4095, 4096, 4097, 32 * 1024, 32 * 4096 + 5, 300_001, 65_536, 1 << 20,
+             3 * 32 * 4096, 777, 16, 5_000_000]
+    kinds = [("t4", "gauss", "laplace", "laplace_outliers", "relu_t4", "uniform_bytes")[i % 6]
+             for i in range(len(sizes))]
+    return inputs.make_shards(sizes, kinds, [50 + i for i in range(len(sizes))], device)
+
+
+def _host(t):
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("cs", [128, 1024, 4096])
+def test_batch_per_shard_lut_matches_oracle(qlc, cs):
+    _, shards = _mixed()
+    b = qlc.Batch(shards, cs, schemes=(1,))
+    b.encode()
+    b.decode()
+    torch.cuda.synchronize()
+    b.check()
+    cb = _host(b.c_bytes)
+    for i, x in enumerate(shards):
+        xh = _host(x)
+        want = oracle.encode(xh, scheme_id=1, chunk_symbols=cs)
+        got = _host(b.container(i))[: cb[i]]
+        assert cb[i] == want.size and np.array_equal(got, want), i
+        assert np.array_equal(_host(b.output(i)), xh), i
+    assert _host(b.n_out).tolist() == [s.numel() for s in shards]
+
+
+def test_batch_shared_lut_and_scheme_choice(qlc):
+    _, shards = _mixed()
+    # shared LUT from the aggregate histogram (an a-priori LUT per tensor type)
+    b = qlc.Batch(shards, 1024, schemes=(1,), shared_lut=True)
+    b.encode()
+    b.decode()
+    torch.cuda.synchronize()
+    b.check()
+    allx = np.concatenate([_host(x) for x in shards])
+    sor, _ = oracle.rank(oracle.histogram(allx))
+    cb = _host(b.c_bytes)
+    for i, x in enumerate(shards):
+        want = oracle.encode(_host(x), scheme_id=1, sym_of_rank=sor, chunk_symbols=1024)
+        assert np.array_equal(_host(b.container(i))[: cb[i]], want), i
+        assert np.array_equal(_host(b.output(i)), _host(x)), i
+    # per shard, the better of Table 1 and Table 2 (Section 6)
+    b = qlc.Batch(shards, 4096, schemes=(1, 2))
+    b.encode()
+    b.decode()
+    torch.cuda.synchronize()
+    b.check()
+    cb = _host(b.c_bytes)
+    for i, x in enumerate(shards):
+        xh = _host(x)
+        h = oracle.histogram(xh)
+        sid = 1 if oracle.code_bits(h, oracle.scheme(1)) <= oracle.code_bits(h, oracle.scheme(2)) else 2
+        want = oracle.encode(xh, scheme_id=sid, chunk_symbols=4096)
+        assert np.array_equal(_host(b.container(i))[: cb[i]], want), i
+        assert np.array_equal(_host(b.output(i)), xh), i
+
+
+def test_batch_equals_single_tensor_path(qlc):
+    _, shards = _mixed()
+    b = qlc.Batch(shards, 4096)
+    b.encode()
+    torch.cuda.synchronize()
+    b.check()
+    for i, x in enumerate(shards):
+        if x.numel() == 0:
+            continue
+        c = qlc.Codec(x.numel(), 4096, 1)
+        out = c.new_container()
+        c.encode_into(x, out)
+        torch.cuda.synchronize()
+        n = int(c.out_bytes.item())
+        assert torch.equal(out[:n], b.container(i)[:n]), i
+
+
+def test_graph_replay_on_new_data(qlc):
+    arena, shards = _mixed()
+    b = qlc.Batch(shards, 2048)
+    b.capture()
+    for rnd in range(2):
+        for i, x in enumerate(shards):  # new contents in the same buffers
+            if x.numel():
+                x.copy_(inputs.make_e4m3("t4", x.numel(), seed=900 + 31 * rnd + i, device="cuda"))
+        b.decoded.fill_(0xEE)
+        b.replay("encode")
+        b.replay("decode")
+        torch.cuda.synchronize()
+        b.check()
+        cb = _host(b.c_bytes)
+        for i in (1, 8, 9, 15):
+            xh = _host(shards[i])
+            want = oracle.encode(xh, scheme_id=1, chunk_symbols=2048)
+            assert np.array_equal(_host(b.container(i))[: cb[i]], want)
+        for i, x in enumerate(shards):
+            assert torch.equal(b.output(i), x), i
+
+
+def test_batch_decode_isolates_a_corrupt_shard(qlc):
+    _, shards = _mixed()
+    b = qlc.Batch(shards, 1024)
+    b.encode()
+    torch.cuda.synchronize()
+    b.check()
+    bad = 9
+    c = b.container(bad)
+    c[400] ^= 0xFF                                    # shard 9's index (chunk_bits[0])
+    b.decoded.zero_()
+    b.decode()
+    torch.cuda.synchronize()
+    st = int(b.status.item())
+    b.status.zero_()
+    ost, _, _ = oracle.decode(_host(c)[: int(b.c_bytes[bad].item())])
+    assert st == ost
+    for i, x in enumerate(shards):
+        if i != bad:
+            assert torch.equal(b.output(i), x), i
+
+
+def _full_batch_check(qlc, shards, cs, shared, sample):
+    b = qlc.Batch(shards, cs, schemes=(1,), shared_lut=shared)
+    b.capture()
+    b.replay("encode")
+    b.replay("decode")
+    torch.cuda.synchronize()
+    b.check()
+    cb = _host(b.c_bytes)
+    for i, x in enumerate(shards):
+        assert torch.equal(b.output(i), x), i
+    sor = None
+    if shared:
+        h = np.zeros(256, np.uint64)
+        for x in shards:
+            h += torch.bincount(x, minlength=256).cpu().numpy().astype(np.uint64)
+        sor, _ = oracle.rank(h)
+    for i in sample:
+        xh = _host(shards[i])
+        want = oracle.encode(xh, scheme_id=1, sym_of_rank=sor, chunk_symbols=cs)
+        assert np.array_equal(_host(b.container(i))[: cb[i]], want), i
+    return b
+
+
+def test_full_size_batched_1152_shards(qlc):
+    """1152 shards, 64 KiB - 16 MiB log-uniform, t4 / gauss / laplace, per-shard
+    LUTs, one graph per direction; every shard round-trips on the device and
+    sampled shards match the oracle byte for byte."""
+    arena, shards = inputs.cfg3_batch("cuda")
+    sizes = [x.numel() for x in shards]
+    sample = [int(np.argmin(sizes)), int(np.argmax(sizes)), 0, 1, 2, 577, 1151]
+    b = _full_batch_check(qlc, shards, 4096, False, sample)
+    total_c = int(b.c_bytes.sum().item())
+    assert total_c < sum(sizes)                       # it compresses
+
+
+def test_full_size_batched_large_shared_and_per_shard(qlc):
+    """64 x 64 MiB Laplace with 1% outliers: shared global LUT and per-shard LUTs."""
+    arena, shards = inputs.cfg4_batch("cuda")
+    _full_batch_check(qlc, shards, 4096, True, [0, 63])
+    _full_batch_check(qlc, shards, 4096, False, [31])
