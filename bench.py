@@ -168,6 +168,102 @@ def run_reference(args):
     return 0
 
 
+def batched_leg(dev, steps: int, warmup: int, peak: float):
+    """The batched workload (1152 shards, 64 KiB - 16 MiB, t4 / gauss / laplace,
+    per-shard LUTs): one CUDA graph per direction with the autotuned launch
+    shape, against per-tensor launches of the plain kernels (eager, and the
+    same launches captured in a graph)."""
+    import torch
+
+    from paper_2602_17849_gb300 import autotune, inputs, qlc
+    arena, shards = inputs.cfg3_batch(dev)
+    torch.cuda.empty_cache()
+    total = sum(x.numel() for x in shards)
+    cfg = autotune.tune(shards)
+    cs = cfg["chunk_symbols"]
+    b = qlc.Batch(shards, cs, launch=(cfg["encode_ctas_per_sm"], cfg["decode_ctas_per_sm"]))
+    b.capture()
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    enc_ms = timed(lambda: b.replay("encode"), steps)
+    dec_ms = timed(lambda: b.replay("decode"), steps)
+    b.check()
+    exact = all(torch.equal(b.output(i), x) for i, x in enumerate(shards))
+    c_total = int(b.c_bytes.sum().item())
+
+    # per-tensor launches of the plain kernels on the same buffers
+    n = len(shards)
+    ws_sizes = [qlc.qlc_encode_workspace_size(x.numel(), cs) for x in shards]
+    ws = torch.zeros(sum(ws_sizes) + 16 * n, dtype=torch.uint8, device=dev)
+    ws_off = [0]
+    for w in ws_sizes:
+        ws_off.append(ws_off[-1] + (w + 15) // 16 * 16)
+    hist = b.hists.view(n, 256)
+    luts = b.luts.view(n, qlc.LUT_BYTES)
+    cbytes = b.c_bytes
+    nout = b.n_out
+    caps = [b.cap_off[i + 1] - b.cap_off[i] for i in range(n)]
+
+    def plain_round_trip():
+        for i, x in enumerate(shards):
+            qlc.qlc_histogram(x, hist[i], stream=stream)
+            qlc.qlc_build_lut(hist[i], SCHEME, luts[i], stream=stream)
+            qlc.qlc_encode(x, luts[i], cs, b.container(i), ws[ws_off[i]:ws_off[i + 1]], cbytes[i:i + 1],
+                           b.status, stream=stream)
+        for i, x in enumerate(shards):
+            qlc.qlc_decode(b.container(i), b.output(i), nout[i:i + 1], b.status, in_bytes=caps[i],
+                           out_cap=x.numel(), stream=stream)
+
+    plain_ms = timed(plain_round_trip, 3)
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream(device=dev)
+    s2.wait_stream(stream)
+    with torch.cuda.graph(g, stream=s2):
+        for i, x in enumerate(shards):
+            cur = torch.cuda.current_stream(dev)
+            qlc.qlc_histogram(x, hist[i], stream=cur)
+            qlc.qlc_build_lut(hist[i], SCHEME, luts[i], stream=cur)
+            qlc.qlc_encode(x, luts[i], cs, b.container(i), ws[ws_off[i]:ws_off[i + 1]], cbytes[i:i + 1],
+                           b.status, stream=cur)
+        for i, x in enumerate(shards):
+            qlc.qlc_decode(b.container(i), b.output(i), nout[i:i + 1], b.status, in_bytes=caps[i],
+                           out_cap=x.numel(), stream=torch.cuda.current_stream(dev))
+    plain_graph_ms = timed(lambda: g.replay(), 3)
+    b.check()
+    exact = exact and all(torch.equal(b.output(i), x) for i, x in enumerate(shards))
+    r = c_total / total
+    rt_ms = enc_ms + dec_ms
+    dec_bytes = total + c_total
+    enc_bytes = 2 * total + c_total  # the histogram reads the input once more
+    return {
+        "workload": "1152 shards, 64 KiB-16 MiB log-uniform, t4/gauss/laplace e4m3, per-shard LUT",
+        "total_bytes": total, "container_bytes": c_total, "compressibility": 1 - r,
+        "tuned": {k: cfg[k] for k in ("chunk_symbols", "encode_ctas_per_sm", "decode_ctas_per_sm")},
+        "encode_ms": enc_ms, "decode_ms": dec_ms, "round_trip_gbs": total / (rt_ms * 1e-3) / 1e9,
+        "decode_gbs": total / (dec_ms * 1e-3) / 1e9,
+        "decode_roofline_frac": dec_bytes / (dec_ms * 1e-3) / 1e9 / peak,
+        "encode_gbs": total / (enc_ms * 1e-3) / 1e9,
+        "encode_roofline_frac": enc_bytes / (enc_ms * 1e-3) / 1e9 / peak,
+        "encode_bytes_counted": "(2 + r) N: histogram read + encode read + container write",
+        "plain_per_tensor_eager_ms": plain_ms, "plain_per_tensor_graph_ms": plain_graph_ms,
+        "batched_ms": rt_ms, "speedup_vs_plain_eager": plain_ms / rt_ms,
+        "speedup_vs_plain_graph": plain_graph_ms / rt_ms, "bit_exact_round_trip": bool(exact),
+        "launches_per_round_trip": {"batched": 7, "plain": 4 * n},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -176,6 +272,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-batched", action="store_true", help="skip the 1152-shard batched leg")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -333,6 +430,8 @@ def main():
         "gpu_launches": 4 * args.steps,
         "clocks": clk.summary(),
     }
+    if not args.no_batched:
+        line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak)
     if rank == 0 and world == 1 and args.cpu_budget > 0:
         xh = x.cpu().numpy()
         b, s = cpu_oracle_roundtrip(xh, budget_s=args.cpu_budget)
