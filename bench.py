@@ -168,7 +168,7 @@ def run_reference(args):
     return 0
 
 
-def batched_leg(dev, steps: int, warmup: int, peak: float):
+def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152):
     """The batched workload (1152 shards, 64 KiB - 16 MiB, t4 / gauss / laplace,
     per-shard LUTs): one CUDA graph per direction with the autotuned launch
     shape, against per-tensor launches of the plain kernels (eager, and the
@@ -176,7 +176,7 @@ def batched_leg(dev, steps: int, warmup: int, peak: float):
     import torch
 
     from paper_2602_17849_gb300 import autotune, inputs, qlc
-    arena, shards = inputs.cfg3_batch(dev)
+    arena, shards = inputs.cfg3_batch(dev, n_shards)
     torch.cuda.empty_cache()
     total = sum(x.numel() for x in shards)
     cfg = autotune.tune(shards)
@@ -248,7 +248,7 @@ def batched_leg(dev, steps: int, warmup: int, peak: float):
     dec_bytes = total + c_total
     enc_bytes = 2 * total + c_total  # the histogram reads the input once more
     return {
-        "workload": "1152 shards, 64 KiB-16 MiB log-uniform, t4/gauss/laplace e4m3, per-shard LUT",
+        "workload": f"{n} shards, 64 KiB-16 MiB log-uniform, t4/gauss/laplace e4m3, per-shard LUT",
         "total_bytes": total, "container_bytes": c_total, "compressibility": 1 - r,
         "tuned": {k: cfg[k] for k in ("chunk_symbols", "encode_ctas_per_sm", "decode_ctas_per_sm")},
         "encode_ms": enc_ms, "decode_ms": dec_ms, "round_trip_gbs": total / (rt_ms * 1e-3) / 1e9,
@@ -273,6 +273,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true", help="skip the 1152-shard batched leg")
+    ap.add_argument("--batched-shards", type=int, default=1152,
+                    help="shards in the batched leg (fewer only for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -431,7 +433,7 @@ def main():
         "clocks": clk.summary(),
     }
     if not args.no_batched:
-        line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak)
+        line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.batched_shards)
     if rank == 0 and world == 1 and args.cpu_budget > 0:
         xh = x.cpu().numpy()
         b, s = cpu_oracle_roundtrip(xh, budget_s=args.cpu_budget)

@@ -314,7 +314,10 @@ __device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in,
           const uint4* src = &s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
           uint8_t* dst = out + rc * cs + off;
           if (off + 16 <= rn) {
-            *reinterpret_cast<uint4*>(dst) = *src;
+            const uint4 v = *src;  // streaming store: the output is written once
+            asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(dst), "r"(v.x), "r"(v.y), "r"(v.z),
+                         "r"(v.w)
+                         : "memory");
           } else {
             const uint8_t* sb = reinterpret_cast<const uint8_t*>(src);
             for (uint32_t b = 0; b < rn - off; b++) dst[b] = sb[b];

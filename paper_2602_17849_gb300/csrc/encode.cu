@@ -27,23 +27,6 @@ constexpr unsigned long long kFlagError = 3ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // 1 s per look-back wait
 
-__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
-  uint32_t d;
-  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-  return d;
-}
-// 0x80000000 >> s with PTX semantics (0 for s >= 32).
-__device__ __forceinline__ uint32_t top_bit_shr(uint32_t s) {
-  uint32_t d;
-  asm("shr.b32 %0, %1, %2;" : "=r"(d) : "r"(0x80000000u), "r"(s));
-  return d;
-}
-
 // Streaming (evict-first) 16-byte store: the container is written once and
 // should not push the input, which pass 2 re-reads, out of L2.
 __device__ __forceinline__ void st_cs_v4(uint4* p, uint4 v) {
@@ -51,12 +34,9 @@ __device__ __forceinline__ void st_cs_v4(uint4* p, uint4 v) {
                : "memory");
 }
 
-// OR v into a shared word when p holds; predicated, so no branch.
-__device__ __forceinline__ void red_or_if(uint32_t saddr, uint32_t v, bool p) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q red.shared.or.b32 [%0], %1;\n\t}" ::"r"(saddr),
-      "r"(v), "r"((uint32_t)p)
-      : "memory");
+// OR v into a shared word.
+__device__ __forceinline__ void red_or(uint32_t saddr, uint32_t v) {
+  asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
@@ -384,30 +364,21 @@ encode_kernel(EncArgs A) {
         total += t;
       }
       const uint32_t pos = base_bit + wpre + incl - L;
-      // Append the pairs to a 64-bit MSB-first accumulator (ahi:alo) in which
-      // the first f bits (1 <= f <= 32) of ahi are taken, g = f - 1.  A pair
-      // is placed with two multiply-adds by 2^(32 - f); each completed word is
-      // OR-ed into the staging buffer under a predicate (no branch).  A
-      // thread's first and last words can be shared with its neighbours.
+      // Place each pair (at most 22 bits, so it touches at most two words)
+      // at its bit position with two unconditional shared ORs; the second is
+      // an OR with 0 when the pair ends inside its first word.  Neighbouring
+      // pairs and threads share words, hence OR.
       {
-        const uint32_t r = pos & 31u;
-        uint32_t g = r ? r - 1 : 31u;
-        uint32_t wa = stage_s + (cur * kStageWords + 4 + (pos >> 5) - win - (r ? 0u : 1u)) * 4;
-        uint32_t ahi = 0, alo = 0;
+        uint32_t p = pos + 32u * (4u - win);  // bit position relative to stage word 0
+        const uint32_t sbase = stage_s + cur * kStageWords * 4;
 #pragma unroll
         for (int k = 0; k < 8; k++) {
-          const uint32_t qq = top_bit_shr(g);
-          ahi = mad_hi(P[k], qq, ahi);
-          alo = mad_lo(P[k], qq, alo);
-          g += L8[k];
-          const bool full = g >= 32;
-          red_or_if(wa, ahi, full && ahi != 0);
-          ahi = full ? alo : ahi;
-          alo = full ? 0u : alo;
-          g -= full ? 32u : 0u;
-          wa += full ? 4u : 0u;
+          const uint32_t r = p & 31u;
+          const uint32_t wa = sbase + (p >> 5) * 4;
+          red_or(wa, P[k] >> r);
+          red_or(wa + 4, __funnelshift_rc(0u, P[k], r));  // P << (32 - r), 0 when r == 0
+          p += L8[k];
         }
-        red_or_if(wa, ahi, ahi != 0);
       }
       __syncthreads();
       // completed 16-byte blocks go out; the partial last block moves to the
