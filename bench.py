@@ -264,6 +264,33 @@ def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152)
     }
 
 
+def serve_leg(dev, seconds: float):
+    """Serving: Poisson arrivals at 20,000 requests/s, half compress and half
+    decompress, sizes log-uniform 4 KiB - 64 MiB of Student-t e4m3 data
+    resident on the device, 8 GiB admission budget (in + out + workspace),
+    continuous batching over 4 streams."""
+    import torch
+
+    from paper_2602_17849_gb300 import serve
+    wl = serve.CudaWorkload(dev, data_bytes=1 << 30, n_containers=128, min_size=4 << 10,
+                            max_size=64 << 20, seed=3000)
+    torch.cuda.empty_cache()
+    reqs, ex, srv, wall = serve.serve_run(dev, rate_hz=20_000, duration_s=seconds, budget_bytes=8 << 30,
+                                          workload=wl, seed=3001)
+    done = [r for r in reqs if r.done is not None]
+    lat = serve.percentiles([r.latency for r in done])
+    raw = sum(r.n_in if r.kind == "compress" else r.n_out for r in done)
+    ok = all(r.status == 0 for r in done)
+    return {
+        "workload": "Poisson 20k req/s, 50/50 compress/decompress, 4 KiB-64 MiB log-uniform t4 e4m3, "
+                    "8 GiB budget, 4 streams",
+        "duration_s": seconds, "requests": len(reqs), "completed": len(done), "rejected": len(srv.rejected),
+        "p50_ms": lat[50] * 1e3 if lat[50] is not None else None,
+        "p99_ms": lat[99] * 1e3 if lat[99] is not None else None,
+        "raw_gbs": raw / wall / 1e9, "offered_gbs": raw / seconds / 1e9, "wall_s": wall, "all_status_ok": ok,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +300,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true", help="skip the 1152-shard batched leg")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg length (0 = skip)")
     ap.add_argument("--batched-shards", type=int, default=1152,
                     help="shards in the batched leg (fewer only for profiling captures)")
     args = ap.parse_args()
@@ -434,6 +462,8 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.batched_shards)
+    if args.serve_seconds > 0:
+        line["serving"] = serve_leg(dev, args.serve_seconds)
     if rank == 0 and world == 1 and args.cpu_budget > 0:
         xh = x.cpu().numpy()
         b, s = cpu_oracle_roundtrip(xh, budget_s=args.cpu_budget)
