@@ -104,8 +104,10 @@ class Server:
     """
 
     def __init__(self, executor, budget_bytes: int, max_in_flight: int = 4,
-                 max_batch: int = 4096, clock: Callable[[], float] = time.perf_counter):
+                 max_batch: int = 4096, clock: Callable[[], float] = time.perf_counter,
+                 on_complete: Optional[Callable[[Request], None]] = None):
         self.ex = executor
+        self.on_complete = on_complete  # sees each result before its memory is reused
         self.arena = Arena(budget_bytes)
         self.max_in_flight = max_in_flight
         self.max_batch = max_batch
@@ -163,6 +165,8 @@ class Server:
                 now = self.clock()
                 for r in batch:
                     r.done = now
+                    if self.on_complete is not None:
+                        self.on_complete(r)
                     self.arena.release(r.out_off)
                     self.completed.append(r)
             else:
@@ -373,12 +377,14 @@ class CudaWorkload:
 
 
 def serve_run(device, rate_hz: float, duration_s: float, budget_bytes: int, workload: CudaWorkload,
-              seed: int, n_streams: int = 4, chunk_symbols: int = 4096):
-    """One Poisson serving run on the GPU; returns (requests, executor, server, wall seconds)."""
+              seed: int, n_streams: int = 4, chunk_symbols: int = 4096, on_complete=None):
+    """One Poisson serving run on the GPU; returns (requests, executor, server, wall seconds).
+    on_complete(request, executor) sees each result before its memory is reused."""
     import torch
     arena_t = torch.empty(budget_bytes, dtype=torch.uint8, device=device)
     ex = CudaExecutor(workload.pool, arena_t, chunk_symbols=chunk_symbols, n_streams=n_streams)
-    srv = Server(ex, budget_bytes, max_in_flight=n_streams)
+    srv = Server(ex, budget_bytes, max_in_flight=n_streams,
+                 on_complete=(lambda r: on_complete(r, ex)) if on_complete else None)
     t0 = time.perf_counter()
     reqs = run_poisson(srv, workload.make_request, rate_hz, duration_s, seed,
                        sleep=lambda s: time.sleep(min(s, 0.0005)))
