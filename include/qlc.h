@@ -127,6 +127,15 @@ qlc_status qlc_build_lut_host(const uint64_t *h_hist, const qlc_scheme *h_scheme
 qlc_status qlc_build_lut_best(const uint64_t *d_hist, const qlc_scheme *h_schemes,
                               int n_schemes, qlc_lut *d_lut, qlc_stream_t stream);
 
+/* Section 8 (future work: tuning the areas, symbols per area and code
+ * lengths): the scheme of the qlc_scheme family with the fewest payload bits
+ * for a histogram, found exhaustively (areas 1..7 complete with
+ * non-decreasing widths, area 8 the remaining ranks, raw or complete).
+ * h_hist: 256 counts (host).  *out receives the scheme (id 1 / 2 when it is
+ * Table 1 / Table 2, else 0); *out_bits (may be NULL) its payload bits.
+ * Host only, synchronous. */
+qlc_status qlc_scheme_search(const uint64_t *h_hist, qlc_scheme *out, uint64_t *out_bits);
+
 /* Worst-case container bytes for n symbols (every code 11 bits); 0 if
  * chunk_symbols is not a multiple of 128 in [128, 4096]. */
 size_t qlc_encoded_size(size_t n, uint32_t chunk_symbols);

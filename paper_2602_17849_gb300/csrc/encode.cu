@@ -11,6 +11,7 @@
 //           of every completed 16-byte block.
 // HBM traffic is one read of the input and one write of the container.
 #include "qlc_common.cuh"
+#include "../../include/qlc_testing.h"
 
 namespace qlc {
 
@@ -472,6 +473,36 @@ qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint3
   const size_t ws_need = qlc_encode_workspace_size(n, chunk_symbols);
   if (ws_bytes < ws_need) return QLC_ERR_CAPACITY;
   if (cudaMemsetAsync(d_ws, 0, ws_need, st) != cudaSuccess) return QLC_ERR_CUDA;
+  EncArgs A = {};
+  A.in = d_in;
+  A.n = n;
+  A.lut = d_lut;
+  A.out = d_out;
+  A.out_bytes = reinterpret_cast<unsigned long long*>(d_out_bytes);
+  A.n_items = n_groups_of(n_chunks);
+  A.cs = chunk_symbols;
+  A.ticket = static_cast<unsigned int*>(d_ws);
+  A.gstat = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(d_ws) + 16);
+  A.status = d_status;
+  encode_kernel<<<enc_grid(A.n_items, nullptr), kEncThreads, 0, st>>>(A);
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+qlc_status qlc_test_encode_stalled_lookback(const uint8_t* d_in, size_t n, const qlc_lut* d_lut,
+                                            uint32_t chunk_symbols, uint8_t* d_out, size_t out_cap,
+                                            void* d_ws, size_t ws_bytes, uint64_t* d_out_bytes,
+                                            uint32_t* d_status, qlc_stream_t stream) {
+  if (!d_in || !d_lut || !d_out || !d_ws || !chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
+  if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0)
+    return QLC_ERR_ARG;
+  const uint64_t n_chunks = (n + chunk_symbols - 1) / chunk_symbols;
+  if (n_groups_of(n_chunks) < 2) return QLC_ERR_ARG;
+  if (out_cap < qlc_encoded_size(n, chunk_symbols)) return QLC_ERR_CAPACITY;
+  const size_t ws_need = qlc_encode_workspace_size(n, chunk_symbols);
+  if (ws_bytes < ws_need) return QLC_ERR_CAPACITY;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(d_ws, 0, ws_need, st) != cudaSuccess) return QLC_ERR_CUDA;
+  if (cudaMemsetAsync(d_ws, 1, 1, st) != cudaSuccess) return QLC_ERR_CUDA;  // group counter = 1
   EncArgs A = {};
   A.in = d_in;
   A.n = n;

@@ -2,6 +2,9 @@
 // kernels of libqlc, plus their C-ABI entry points.
 #include "qlc_common.cuh"
 
+#include <algorithm>
+#include <functional>
+
 namespace qlc {
 
 constexpr int kHistWarps = 8;
@@ -264,6 +267,74 @@ qlc_status qlc_build_lut_host(const uint64_t* h_hist, const qlc_scheme* h_scheme
     h_lut->enc[s] = (uint16_t)lut_entry(h_lut->scheme, r);
     h_lut->dec[r] = (uint8_t)s;
   }
+  return QLC_OK;
+}
+
+// Section 8 leaves the choice of areas, symbols per area and code lengths as
+// future work.  Within the family this library codes (qlc_scheme), the best
+// scheme for a histogram is found exhaustively: areas 1..7 are complete
+// (2^b ranks, b non-decreasing in 0..7), area 8 takes the remaining ranks,
+// either raw (8 bits) or complete when their number is a power of two.  Cost
+// = sum over ranks of count * code length, counts taken in decreasing order.
+qlc_status qlc_scheme_search(const uint64_t* h_hist, qlc_scheme* out, uint64_t* out_bits) {
+  if (!h_hist || !out) return QLC_ERR_ARG;
+  uint64_t c[256];
+  for (int i = 0; i < 256; i++) c[i] = h_hist[i];
+  std::sort(c, c + 256, std::greater<uint64_t>());
+  uint64_t pre[257];
+  pre[0] = 0;
+  for (int i = 0; i < 256; i++) pre[i + 1] = pre[i] + c[i];
+  uint64_t best = ~0ull;
+  uint8_t best_b[8] = {0};
+  uint16_t best_n[8] = {0};
+  uint8_t b[8];
+  // depth-first over b[0] <= b[1] <= ... <= b[6]
+  struct Rec {
+    static void go(int i, uint32_t base, uint64_t cost, uint8_t* b, const uint64_t* pre, uint64_t* best,
+                   uint8_t* best_b, uint16_t* best_n) {
+      if (i == 7) {
+        const uint32_t rem = 256 - base;
+        uint32_t last_bits = 8;
+        if ((rem & (rem - 1)) == 0 && rem <= 128) {  // power of two: complete area
+          uint32_t lb = 0;
+          while ((1u << lb) < rem) lb++;
+          if (lb >= b[6]) last_bits = lb;
+        }
+        const uint64_t total = cost + (3 + last_bits) * (pre[256] - pre[base]);
+        if (total < *best) {
+          *best = total;
+          for (int k = 0; k < 7; k++) {
+            best_b[k] = b[k];
+            best_n[k] = (uint16_t)(1u << b[k]);
+          }
+          best_b[7] = (uint8_t)last_bits;
+          best_n[7] = (uint16_t)rem;
+        }
+        return;
+      }
+      for (uint32_t bi = i ? b[i - 1] : 0; bi <= 7; bi++) {
+        const uint32_t n = 1u << bi;
+        if (base + n > 255) break;  // area 8 keeps at least one rank
+        b[i] = (uint8_t)bi;
+        go(i + 1, base + n, cost + (3 + bi) * (pre[base + n] - pre[base]), b, pre, best, best_b, best_n);
+      }
+    }
+  };
+  Rec::go(0, 0, 0, b, pre, &best, best_b, best_n);
+  qlc_scheme sc = {};
+  for (int i = 0; i < 8; i++) {
+    sc.area_n[i] = best_n[i];
+    sc.area_bits[i] = best_b[i];
+  }
+  sc.id = 0;
+  for (int id = 1; id <= 2; id++) {
+    const qlc_scheme& t = id == 1 ? kTable1 : kTable2;
+    bool same = true;
+    for (int i = 0; i < 8; i++) same = same && t.area_n[i] == sc.area_n[i] && t.area_bits[i] == sc.area_bits[i];
+    if (same) sc.id = (uint8_t)id;
+  }
+  *out = sc;
+  if (out_bits) *out_bits = best;
   return QLC_OK;
 }
 

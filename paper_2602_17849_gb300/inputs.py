@@ -26,7 +26,7 @@ import torch
 E4M3_MAX = 480.0
 BLOCK = 32
 
-KINDS = ("t4", "gauss", "laplace", "laplace_outliers", "relu_t4", "uniform_bytes", "constant")
+KINDS = ("t4", "gauss", "laplace", "laplace_outliers", "relu_t4", "ffn2", "uniform_bytes", "constant")
 
 
 def e4m3_values() -> np.ndarray:
@@ -103,6 +103,12 @@ def _draw(kind: str, n: int, gen: torch.Generator, device) -> torch.Tensor:
             out = 20.0 * torch.randn(n, generator=gen, device=device, dtype=torch.float32)
             x = torch.where(mask, out, x)
         return x
+    if kind == "ffn2":
+        # FFN2-activation-like input (Section 6: one symbol, zero, is far more
+        # frequent than the rest): Student-t(4) activations with 18% of the
+        # elements exactly zero; entropy ~6.13 bits against the paper's 6.11
+        x = _draw("t4", n, gen, device)
+        return torch.where(torch.rand(n, generator=gen, device=device) < 0.18, torch.zeros_like(x), x)
     if kind == "relu_t4":
         # post-nonlinearity (FFN2-like) input: ReLU of Student-t(4) activations,
         # so one symbol (zero) dominates, as Section 6 describes
@@ -114,8 +120,9 @@ def make_e4m3(kind: str, n: int, seed: int, device="cpu", piece: int = 1 << 26) 
     """n seeded synthetic e4m3 bytes (uint8 tensor on `device`).
 
     kinds: t4 (activations), gauss (weights), laplace (gradients),
-    laplace_outliers (Laplace b=1 with 1% N(0, 20^2) outliers), relu_t4
-    (post-ReLU, dominant zero), uniform_bytes (incompressible), constant.
+    laplace_outliers (Laplace b=1 with 1% N(0, 20^2) outliers), ffn2 (18%
+    exact zeros, FFN2-like), relu_t4 (post-ReLU, half zeros), uniform_bytes
+    (incompressible), constant.
     Generated in pieces of `piece` elements (a multiple of 32) so that large
     tensors do not need large fp32 temporaries.
     """

@@ -73,6 +73,8 @@ def _load() -> ctypes.CDLL:
     L.qlc_encode.argtypes = [P, sz, P, u32, P, sz, P, sz, P, P, P]
     L.qlc_decode.argtypes = [P, sz, P, sz, P, P, P]
     L.qlc_peek_header.argtypes = [P, sz, P, P]
+    L.qlc_scheme_search.argtypes = [P, P, P]
+    L.qlc_scheme_search.restype = i32
     u64 = ctypes.c_uint64
     L.qlc_encode_noalloc.argtypes = [P, sz, P, u32, P, sz, P, P, P]
     L.qlc_batch_workspace_size.argtypes = [i32, u64, u32]
@@ -186,6 +188,15 @@ def qlc_build_lut_host(hist, scheme) -> qlc_lut:
     out = qlc_lut()
     _check(lib.qlc_build_lut_host(h, ctypes.byref(s), ctypes.byref(out)), "qlc_build_lut_host")
     return out
+
+
+def qlc_scheme_search(hist):
+    """(best qlc_scheme of the family for this histogram, its payload bits)."""
+    h = (ctypes.c_uint64 * 256)(*[int(v) for v in hist])
+    out = qlc_scheme()
+    bits = ctypes.c_uint64()
+    _check(lib.qlc_scheme_search(h, ctypes.byref(out), ctypes.byref(bits)), "qlc_scheme_search")
+    return out, int(bits.value)
 
 
 def qlc_encoded_size(n: int, chunk_symbols: int = 4096) -> int:

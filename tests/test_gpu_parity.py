@@ -192,3 +192,17 @@ def test_full_1mib_tensor(qlc):
     code_only = 1 - oracle.code_bits(h, oracle.scheme(1)) / (8 * x.size)
     container = 1 - r["cont"].size / x.size
     assert abs(code_only - container) < 0.001           # index overhead < 0.1 pp
+
+
+@pytest.mark.parametrize("kind", ["ffn2", "t4"])
+def test_searched_scheme_on_gpu_matches_oracle(qlc, kind):
+    """A scheme from the exhaustive search (not one of the printed tables)
+    codes bit-exactly on the GPU: histogram, LUT, container and decode."""
+    x = inputs.make_e4m3(kind, 3 * 32 * 1024 + 555, seed=21).numpy()
+    h = oracle.histogram(x)
+    sc, _ = qlc.qlc_scheme_search(h)
+    area = (np.array(list(sc.area_n), np.uint16), np.array(list(sc.area_bits), np.uint8))
+    r = _gpu_pipeline(qlc, x, sc, 1024)
+    want = oracle.encode(x, scheme_id=int(sc.id), area=area, chunk_symbols=1024)
+    assert np.array_equal(r["cont"], want)
+    assert np.array_equal(r["y"], x)

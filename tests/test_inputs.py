@@ -60,6 +60,7 @@ def test_deterministic_by_seed():
 
 @pytest.mark.parametrize("kind,lo,hi", [("t4", 6.3, 6.9), ("gauss", 6.1, 6.7), ("laplace", 6.4, 7.0),
                                         ("laplace_outliers", 6.6, 7.2), ("relu_t4", 3.0, 6.3),
+                                        ("ffn2", 5.95, 6.3),
                                         ("uniform_bytes", 7.99, 8.0)])
 def test_stand_in_entropies(kind, lo, hi):
     """Entropies of the stand-ins bracket the paper's 6.69 bits (FFN1, Section 4)

@@ -34,7 +34,7 @@ def test_round_trip_sizes(n, cs):
     assert st == oracle.OK and m == n and np.array_equal(out, x)
 
 
-@pytest.mark.parametrize("kind", ["t4", "gauss", "laplace", "laplace_outliers", "relu_t4",
+@pytest.mark.parametrize("kind", ["t4", "gauss", "laplace", "laplace_outliers", "relu_t4", "ffn2",
                                   "uniform_bytes", "constant"])
 @pytest.mark.parametrize("sid", [1, 2])
 def test_round_trip_synthetic(kind, sid):
@@ -149,6 +149,24 @@ def test_paper_ordering_on_synthetic_activations():
     qlc = 1 - oracle.code_bits(h, oracle.scheme(1)) / (8 * x.size)
     assert ideal > huff > qlc > 0.10
     assert 0.12 < ideal < 0.22
+
+
+def test_adaptation_ordering_on_ffn2_stand_in():
+    """Section 6: on an FFN2-like PMF (one dominant symbol, zero) the adapted
+    scheme (Table 2) beats Table 1 by a few percentage points and stays a few
+    points below Huffman; entropy bound > Huffman > Table 2 > Table 1.  The
+    paper's own 23.6 / 23.2 / 19.0 / 16.7 % are measured on Gemma-2B tensors
+    (parity unpinned); the stand-in must keep the ordering and the gaps' signs."""
+    x = inputs.make_e4m3("ffn2", 1 << 20, seed=0).numpy()
+    h = oracle.histogram(x)
+    n = x.size
+    ideal = (8 - oracle.entropy(h)) / 8
+    huff = 1 - oracle.huffman_bits(h) / (8 * n)
+    t1 = 1 - oracle.code_bits(h, oracle.scheme(1)) / (8 * n)
+    t2 = 1 - oracle.code_bits(h, oracle.scheme(2)) / (8 * n)
+    assert ideal > huff > t2 > t1
+    assert 0.01 < t2 - t1 < 0.05 and 0.02 < huff - t2 < 0.07
+    assert int(np.argmax(h)) == 0                     # zero is the dominant symbol
 
 
 def test_container_layout_and_index():
