@@ -18,8 +18,9 @@ namespace qlc {
 constexpr int kEncThreads = 256;
 constexpr int kEncWarps = kEncThreads / 32;
 constexpr int kEncCtasPerSm = 3;
-constexpr int kTile = kEncThreads * 16;
-constexpr int kStageWords = 4 + 4 + (kTile * kMaxCode + 31) / 32 + 4;
+constexpr int kSub = 32 * 16;  // symbols a warp packs per step (16 per lane)
+// per-warp staging buffer: 4 guard words, 4 carry words, one step's words, 4 spare
+constexpr int kWStage = 4 + 4 + (kSub * kMaxCode + 31) / 32 + 4;
 constexpr int kPass1Unroll = 8;
 
 constexpr unsigned long long kFlagAgg = 1ull << 62;
@@ -163,9 +164,11 @@ __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm)
 encode_kernel(EncArgs A) {
   __shared__ uint32_t s_enc[256];  // MSB-aligned codeword | length, by symbol
   __shared__ uint8_t s_len[256];
-  __shared__ __align__(16) uint32_t s_stage[2][kStageWords];  // ping-pong, 4 guard words in front
+  __shared__ __align__(16) uint32_t s_stage[kEncWarps][2][kWStage];  // per-warp ping-pong
   __shared__ uint32_t s_chunk_bits[kGroupChunks];
-  __shared__ uint32_t s_warp[kEncWarps];
+  __shared__ uint32_t s_chunk_start[kGroupChunks + 1];  // group-relative bit of each chunk
+  __shared__ __align__(16) uint4 s_seam[kGroupChunks][2];  // a chunk's first / last 16-byte block
+  __shared__ uint32_t s_seam_idx[kGroupChunks][2];         // their block index, ~0u if none
   __shared__ unsigned long long s_item, s_first, s_excl;
   __shared__ const uint8_t* s_in;
   __shared__ uint64_t s_n;
@@ -177,10 +180,10 @@ encode_kernel(EncArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t cs = A.cs;
   const uint64_t group_syms = (uint64_t)kGroupChunks * cs;
-  const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(&s_stage[0][0]);
+  const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(&s_stage[warp][0][0]);
   const uint64_t n_items = A.descs ? A.item_base[A.n_shards] : A.n_items;
   const qlc_lut* cur_lut = nullptr;
-  for (int i = tid; i < 2 * kStageWords; i += kEncThreads) (&s_stage[0][0])[i] = 0;
+  for (int i = tid; i < kEncWarps * 2 * kWStage; i += kEncThreads) (&s_stage[0][0][0])[i] = 0;
 
   while (true) {
     __syncthreads();
@@ -280,7 +283,17 @@ encode_kernel(EncArgs A) {
 
     // ---- look-back: this group's byte offset in the payload
     if (warp == 0) {
-      const uint32_t gbits = warp_sum_u32(s_chunk_bits[lane]);
+      const uint32_t cb = s_chunk_bits[lane];
+      uint32_t incl = cb;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      s_chunk_start[lane] = incl - cb;
+      if (lane == 31) s_chunk_start[32] = incl;
+      s_seam_idx[lane][0] = s_seam_idx[lane][1] = ~0u;
+      const uint32_t gbits = __shfl_sync(0xffffffffu, incl, 31);
       const uint64_t gbytes = align16((gbits + 7) / 8);
       bool err = false;
       const unsigned long long excl = lookback(A.gstat, item, s_first, gbytes, lane, &err);
@@ -302,112 +315,144 @@ encode_kernel(EncArgs A) {
     if (s_err) continue;
     uint4* dst = reinterpret_cast<uint4*>(payload + s_excl);
 
-    // ---- pass 2: pack the group's codewords, tile by tile.  Two staging
-    // buffers alternate between tiles: a tile packs into one while the
-    // completed 16-byte blocks of the previous tile leave from the other, so
-    // each tile needs two barriers.
-    uint32_t base_bit = 0;  // group-relative bit position of the tile start
-    uint32_t win = 0;       // group-relative word index of stage word 4 (multiple of 4)
-    int cur = 0;            // staging buffer of this tile
-    uint4 qn = make_uint4(0, 0, 0, 0);
-    {
-      const uint64_t my = gbeg + (uint64_t)tid * 16;
-      if (my + 16 <= gend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + my));
-    }
-    for (uint64_t tbeg = gbeg; tbeg < gend; tbeg += kTile) {
-      const uint64_t my = tbeg + (uint64_t)tid * 16;
-      uint4 q = qn;
-      int cnt = 16;
-      if (my + 16 > gend) {  // ragged end of the last group only
-        cnt = my < gend ? (int)(gend - my) : 0;
-        uint32_t w[4] = {0, 0, 0, 0};
-        for (int j = 0; j < cnt; j++) w[j >> 2] |= (uint32_t)in[my + j] << (8 * (j & 3));
-        q = make_uint4(w[0], w[1], w[2], w[3]);
-      }
+    // ---- pass 2: each warp packs its own chunks (w, w+8, w+16, w+24), 512
+    // symbols per step, with warp scans only: a chunk's start bit is known
+    // from pass 1.  Completed 16-byte blocks go straight out, except the 16-
+    // byte blocks a chunk shares with its neighbours, which wait in s_seam.
+    for (uint32_t c = warp; c < kGroupChunks; c += kEncWarps) {
+      const uint64_t cbeg = gbeg + (uint64_t)c * cs;
+      if (cbeg >= gend) break;
+      const uint64_t cend = min(cbeg + cs, gend);
+      const uint32_t S = s_chunk_start[c], E = s_chunk_start[c + 1];
+      uint32_t base_bit = S;            // group-relative bit of this step's first symbol
+      uint32_t win = (S >> 5) & ~3u;    // group-relative word of stage word 4
+      int cur = 0;
+      uint4 qn = make_uint4(0, 0, 0, 0);
       {
-        const uint64_t nx = my + kTile;
-        if (nx + 16 <= gend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + nx));
+        const uint64_t my = cbeg + (uint64_t)lane * 16;
+        if (my + 16 <= cend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + my));
       }
-      // 16 codewords -> 8 pairs: MSB-aligned (at most 22 bits), lengths in P/L.
-      // An entry is codeword << (32 - len) | len, so e & 31 == len.
-      uint32_t P[8], L8[8];
-      uint32_t L = 0;
-      const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
-      uint32_t e[16];
-      if (cnt == 16) {
+      for (uint64_t tbeg = cbeg; tbeg < cend; tbeg += kSub) {
+        const uint64_t my = tbeg + (uint64_t)lane * 16;
+        uint4 q = qn;
+        int cnt = 16;
+        if (my + 16 > cend) {  // ragged end of the last chunk only
+          cnt = my < cend ? (int)(cend - my) : 0;
+          uint32_t w[4] = {0, 0, 0, 0};
+          for (int j = 0; j < cnt; j++) w[j >> 2] |= (uint32_t)in[my + j] << (8 * (j & 3));
+          q = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        {
+          const uint64_t nx = my + kSub;
+          if (nx + 16 <= cend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + nx));
+        }
+        // 16 codewords -> 8 pairs: MSB-aligned (at most 22 bits), lengths in P/L8.
+        // An entry is codeword << (32 - len) | len, so e & 31 == len.
+        uint32_t P[8], L8[8];
+        uint32_t L = 0;
+        const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+        uint32_t e[16];
+        if (cnt == 16) {
 #pragma unroll
-        for (int j = 0; j < 16; j++) e[j] = s_enc[__byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3))];
-      } else {
+          for (int j = 0; j < 16; j++) e[j] = s_enc[__byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3))];
+        } else {
 #pragma unroll
-        for (int j = 0; j < 16; j++) e[j] = j < cnt ? s_enc[__byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3))] : 0u;
-      }
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const uint32_t e0 = e[2 * k], e1 = e[2 * k + 1];
-        P[k] = (e0 & ~31u) | __funnelshift_r(e1 & ~31u, 0u, e0);  // second code right after the first
-        L8[k] = (e0 + e1) & 31u;  // the two lengths; code bits sit above bit 20
-        L += L8[k];
-      }
-      // block exclusive scan of L
-      uint32_t incl = L;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      if (lane == 31) s_warp[warp] = incl;
-      __syncthreads();
-      uint32_t wpre = 0, total = 0;
-#pragma unroll
-      for (int w = 0; w < kEncWarps; w++) {
-        const uint32_t t = s_warp[w];
-        wpre += w < warp ? t : 0u;
-        total += t;
-      }
-      const uint32_t pos = base_bit + wpre + incl - L;
-      // Place each pair (at most 22 bits, so it touches at most two words)
-      // at its bit position with two unconditional shared ORs; the second is
-      // an OR with 0 when the pair ends inside its first word.  Neighbouring
-      // pairs and threads share words, hence OR.
-      {
-        uint32_t p = pos + 32u * (4u - win);  // bit position relative to stage word 0
-        const uint32_t sbase = stage_s + cur * kStageWords * 4;
+          for (int j = 0; j < 16; j++) e[j] = j < cnt ? s_enc[__byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3))] : 0u;
+        }
 #pragma unroll
         for (int k = 0; k < 8; k++) {
-          const uint32_t r = p & 31u;
-          const uint32_t wa = sbase + (p >> 5) * 4;
-          red_or(wa, P[k] >> r);
-          red_or(wa + 4, __funnelshift_rc(0u, P[k], r));  // P << (32 - r), 0 when r == 0
-          p += L8[k];
+          const uint32_t e0 = e[2 * k], e1 = e[2 * k + 1];
+          P[k] = (e0 & ~31u) | __funnelshift_r(e1 & ~31u, 0u, e0);  // second code right after the first
+          L8[k] = (e0 + e1) & 31u;  // the two lengths; code bits sit above bit 20
+          L += L8[k];
         }
+        uint32_t incl = L;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        // Place each pair (at most 22 bits: at most two words) at its bit
+        // position with two unconditional shared ORs; the second ORs 0 when
+        // the pair ends inside its first word.  Neighbouring pairs and lanes
+        // share words, hence OR.
+        {
+          uint32_t p = base_bit + incl - L + 32u * (4u - win);  // bit relative to stage word 0
+          const uint32_t sbase = stage_s + cur * kWStage * 4;
+#pragma unroll
+          for (int k = 0; k < 8; k++) {
+            const uint32_t r = p & 31u;
+            const uint32_t wa = sbase + (p >> 5) * 4;
+            red_or(wa, P[k] >> r);
+            red_or(wa + 4, __funnelshift_rc(0u, P[k], r));  // P << (32 - r), 0 when r == 0
+            p += L8[k];
+          }
+        }
+        __syncwarp();
+        // completed 16-byte blocks go out (the chunk's first block, when it is
+        // shared with the previous chunk, goes to the seam); the partial last
+        // block moves to the other buffer; what was read is zeroed for reuse
+        const uint32_t end_bit = base_bit + total;
+        const uint32_t nblk = ((end_bit >> 5) - win) / 4;
+        uint32_t* sb = &s_stage[warp][cur][4];
+        for (uint32_t b = lane; b < nblk; b += 32) {
+          uint4* s4 = reinterpret_cast<uint4*>(&sb[4 * b]);
+          const uint4 v = *s4;
+          const uint32_t blk = win / 4 + b;
+          const uint4 be = make_uint4(bswap32(v.x), bswap32(v.y), bswap32(v.z), bswap32(v.w));
+          if (blk == (S >> 7) && (S & 127u)) {
+            s_seam[c][0] = be;
+            s_seam_idx[c][0] = blk;
+          } else {
+            st_cs_v4(&dst[blk], be);
+          }
+          *s4 = make_uint4(0, 0, 0, 0);
+        }
+        if (lane < 4) {
+          s_stage[warp][cur ^ 1][4 + lane] = sb[4 * nblk + lane];
+          sb[4 * nblk + lane] = 0;
+        }
+        win += 4 * nblk;
+        base_bit = end_bit;
+        cur ^= 1;
+        __syncwarp();
       }
-      __syncthreads();
-      // completed 16-byte blocks go out; the partial last block moves to the
-      // other buffer; everything read here is zeroed for reuse
-      const uint32_t end_bit = base_bit + total;
-      const uint32_t nblk = ((end_bit >> 5) - win) / 4;
-      uint32_t* sb = &s_stage[cur][4];
-      for (uint32_t b = tid; b < nblk; b += kEncThreads) {
-        uint4* s4 = reinterpret_cast<uint4*>(&sb[4 * b]);
-        const uint4 v = *s4;
-        st_cs_v4(&dst[win / 4 + b], make_uint4(bswap32(v.x), bswap32(v.y), bswap32(v.z), bswap32(v.w)));
-        *s4 = make_uint4(0, 0, 0, 0);
+      // the chunk's partial last block (shared with the next chunk, or the
+      // group's zero-padded end) goes to the seam; the buffer is left zeroed
+      if (lane == 0) {
+        uint32_t* cb = &s_stage[warp][cur][4];
+        if (E & 127u) {
+          s_seam[c][1] = make_uint4(bswap32(cb[0]), bswap32(cb[1]), bswap32(cb[2]), bswap32(cb[3]));
+          s_seam_idx[c][1] = E >> 7;
+        }
+        cb[0] = cb[1] = cb[2] = cb[3] = 0;
       }
-      if (tid < 4) {
-        s_stage[cur ^ 1][4 + tid] = sb[4 * nblk + tid];
-        sb[4 * nblk + tid] = 0;
-      }
-      win += 4 * nblk;
-      base_bit = end_bit;
-      cur ^= 1;
+      __syncwarp();
     }
     __syncthreads();
-    // last, partial 16-byte block of the group (zero bits after the end)
-    if (tid == 0) {
-      uint32_t* c = &s_stage[cur][4];
-      if (base_bit & 127u)
-        dst[win / 4] = make_uint4(bswap32(c[0]), bswap32(c[1]), bswap32(c[2]), bswap32(c[3]));
-      c[0] = c[1] = c[2] = c[3] = 0;
+    // Seams: lane l writes the block holding chunk l's end, OR-ed with the
+    // blocks of chunk l+1 that fall in the same 16 bytes.  A chunk shorter
+    // than a block (only the last chunk of a tensor) is merged by the lane of
+    // the chunk before it.
+    if (warp == 0) {
+      const uint32_t i1 = s_seam_idx[lane][1];
+      const bool mine = i1 != ~0u && !(lane > 0 && s_seam_idx[lane - 1][1] == i1);
+      if (mine) {
+        uint4 v = s_seam[lane][1];
+        if (lane + 1 < kGroupChunks) {
+          for (int k = 0; k < 2; k++) {
+            if (s_seam_idx[lane + 1][k] == i1) {
+              const uint4 u = s_seam[lane + 1][k];
+              v.x |= u.x;
+              v.y |= u.y;
+              v.z |= u.z;
+              v.w |= u.w;
+            }
+          }
+        }
+        st_cs_v4(&dst[i1], v);
+      }
     }
   }
 }
