@@ -41,6 +41,14 @@ __device__ __forceinline__ void red_or(uint32_t saddr, uint32_t v) {
   asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
 }
 
+// OR v into a shared word when nb >= 32 (predicated, no branch).
+__device__ __forceinline__ void red_or_if_full(uint32_t saddr, uint32_t v, uint32_t nb) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ge.u32 q, %2, 32;\n\t@q red.shared.or.b32 [%0], %1;\n\t}" ::"r"(saddr),
+      "r"(v), "r"(nb)
+      : "memory");
+}
+
 __device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -52,15 +60,22 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
   return v;
 }
 
-// Sum of the code lengths of 16 symbols (s_len: one byte per symbol).
-__device__ __forceinline__ uint32_t len16(const uint8_t* s_len, uint4 q) {
+// The encoder table holds one copy per lane (entry s of lane l at word
+// 32 s + l), so the 32 lanes of a lookup always hit 32 different banks.
+// tab points at this lane's copy.
+__device__ __forceinline__ uint32_t enc_entry(const uint32_t* tab, uint32_t s) { return tab[s << 5]; }
+
+// Sum of the encoder entries of 16 symbols.  An entry is
+// codeword << (32 - len) | len with len <= 11, so its bits below 21 are the
+// length alone, and the low 21 bits of a sum of entries are the sum of the
+// lengths as long as that stays below 2^21.
+__device__ __forceinline__ uint32_t entry_sum16(const uint32_t* tab, uint4 q) {
   const uint32_t w[4] = {q.x, q.y, q.z, q.w};
   uint32_t s = 0;
 #pragma unroll
   for (int k = 0; k < 4; k++)
 #pragma unroll
-    for (int j = 0; j < 4; j += 2)
-      s += s_len[__byte_perm(w[k], 0, 0x4440 + j)] + s_len[__byte_perm(w[k], 0, 0x4441 + j)];
+    for (int j = 0; j < 4; j++) s += enc_entry(tab, __byte_perm(w[k], 0, 0x4440 + j));
   return s;
 }
 
@@ -160,10 +175,122 @@ __device__ __forceinline__ int shard_of(const unsigned long long* item_base, int
   return lo;
 }
 
+// Packing state of one warp within one chunk.  The warp appends 512
+// symbols per step (16 per lane, in lane order) to the chunk's bit stream in a
+// per-warp staging window; completed 16-byte blocks go to the payload, except
+// the chunk's first block when it is shared with the previous chunk, which
+// goes to the chunk's seam slot.
+struct Packer {
+  const uint32_t* tab;   // this lane's copy of the encoder table
+  uint32_t* stage;       // the warp's two staging buffers
+  uint32_t stage_s;      // their shared address
+  uint4* dst;            // the group's payload
+  uint32_t seam_s;       // shared address of the chunk's seam slot [0]
+  uint32_t seam_idx_s;   // and of its block index
+  uint32_t seam_blk;     // block shared with the previous chunk, ~0u if none
+  uint32_t base_bit;     // group-relative bit of the step's first symbol
+  uint32_t win;          // group-relative word held at stage word 4 (a multiple of 4)
+  uint32_t cur;          // staging buffer in use
+  int lane;
+
+  // Moves block b (< nblk) of the current buffer out and zeroes it; branch-free.
+  __device__ __forceinline__ void put_block(uint32_t b, uint32_t nblk, const uint32_t* sb) const {
+    const uint32_t blk = win / 4 + b;
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sb) + 16u * b;
+    asm volatile(
+        "{\n\t"
+        ".reg .pred p, s, g;\n\t"
+        ".reg .b32 a0, a1, a2, a3, z;\n\t"
+        "mov.b32 z, 0;\n\t"
+        "setp.lt.u32 p, %0, %1;\n\t"
+        "setp.eq.and.u32 s, %2, %3, p;\n\t"
+        "setp.ne.and.u32 g, %2, %3, p;\n\t"
+        "@p ld.shared.v4.u32 {a0, a1, a2, a3}, [%4];\n\t"
+        "@p st.shared.v4.u32 [%4], {z, z, z, z};\n\t"
+        "prmt.b32 a0, a0, 0, 0x0123;\n\t"
+        "prmt.b32 a1, a1, 0, 0x0123;\n\t"
+        "prmt.b32 a2, a2, 0, 0x0123;\n\t"
+        "prmt.b32 a3, a3, 0, 0x0123;\n\t"
+        "@g st.global.cs.v4.u32 [%5], {a0, a1, a2, a3};\n\t"
+        "@s st.shared.v4.u32 [%6], {a0, a1, a2, a3};\n\t"
+        "@s st.shared.u32 [%7], %2;\n\t"
+        "}" ::"r"(b),
+        "r"(nblk), "r"(blk), "r"(seam_blk), "r"(sa), "l"(dst + blk), "r"(seam_s), "r"(seam_idx_s)
+        : "memory");
+  }
+
+  template <bool kRagged>
+  __device__ __forceinline__ void step(uint4 q, int cnt) {
+    // 16 codewords -> 8 pairs: MSB-aligned (at most 22 bits), lengths in L8.
+    // An entry is codeword << (32 - len) | len, so e & 31 == len.
+    const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
+    uint32_t e[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+      e[j] = enc_entry(tab, __byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3)));
+      if (kRagged) e[j] = j < cnt ? e[j] : 0u;
+    }
+    uint32_t P[8], L8[8];
+    uint32_t L = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const uint32_t e0 = e[2 * k], e1 = e[2 * k + 1];
+      P[k] = (e0 & ~31u) | __funnelshift_r(e1 & ~31u, 0u, e0);  // second code right after the first
+      L8[k] = (e0 + e1) & 31u;  // the two lengths; code bits sit above bit 20
+      L += L8[k];
+    }
+    uint32_t incl = L;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    // Each lane packs its pairs into a two-word accumulator (hi:lo, hi
+    // first) that starts at the lane's bit offset within a word, and ORs each
+    // completed word into the stage.  Only a lane's first and last words can
+    // be shared with the neighbouring lanes, hence OR.
+    {
+      const uint32_t p = base_bit + incl - L + 32u * (4u - win);  // bit relative to stage word 0
+      uint32_t wa = stage_s + cur * kWStage * 4 + (p >> 5) * 4;
+      uint32_t nb = p & 31u;  // bits in hi
+      uint32_t hi = 0;
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        hi |= P[k] >> nb;
+        const uint32_t lo = __funnelshift_rc(0u, P[k], nb);  // P << (32 - nb), 0 when nb == 0
+        nb += L8[k];                                         // at most 31 + 22
+        red_or_if_full(wa, hi, nb);
+        const uint32_t full = nb >> 5;
+        hi = full ? lo : hi;
+        wa += full * 4;
+        nb &= 31u;
+      }
+      red_or(wa, hi);  // the partial last word (0 adds nothing)
+    }
+    __syncwarp();
+    // completed 16-byte blocks go out (at most 45 per step: 128 carried +
+    // 512 * 11 new bits); the partial last block moves to the other buffer
+    const uint32_t end_bit = base_bit + total;
+    const uint32_t nblk = ((end_bit >> 5) - win) / 4;
+    uint32_t* sb = stage + cur * kWStage + 4;
+    put_block(lane, nblk, sb);
+    if (nblk > 32) put_block(lane + 32, nblk, sb);
+    if (lane < 4) {
+      stage[(cur ^ 1) * kWStage + 4 + lane] = sb[4 * nblk + lane];
+      sb[4 * nblk + lane] = 0;
+    }
+    seam_blk = ~0u;  // only a chunk's first step can complete its first block
+    win += 4 * nblk;
+    base_bit = end_bit;
+    cur ^= 1;
+    __syncwarp();
+  }
+};
+
 __global__ void __launch_bounds__(kEncThreads, kEncCtasPerSm)
 encode_kernel(EncArgs A) {
-  __shared__ uint32_t s_enc[256];  // MSB-aligned codeword | length, by symbol
-  __shared__ uint8_t s_len[256];
+  __shared__ __align__(16) uint32_t s_enc[256 * 32];  // codeword << (32 - len) | len, one copy per lane
   __shared__ __align__(16) uint32_t s_stage[kEncWarps][2][kWStage];  // per-warp ping-pong
   __shared__ uint32_t s_chunk_bits[kGroupChunks];
   __shared__ uint32_t s_chunk_start[kGroupChunks + 1];  // group-relative bit of each chunk
@@ -181,6 +308,7 @@ encode_kernel(EncArgs A) {
   const uint32_t cs = A.cs;
   const uint64_t group_syms = (uint64_t)kGroupChunks * cs;
   const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(&s_stage[warp][0][0]);
+  const uint32_t* tab = &s_enc[lane];
   const uint64_t n_items = A.descs ? A.item_base[A.n_shards] : A.n_items;
   const qlc_lut* cur_lut = nullptr;
   for (int i = tid; i < kEncWarps * 2 * kWStage; i += kEncThreads) (&s_stage[0][0][0])[i] = 0;
@@ -233,8 +361,12 @@ encode_kernel(EncArgs A) {
         cur_lut = nullptr;
         continue;
       }
-      s_enc[tid] = (code << (32 - len)) | len;
-      s_len[tid] = (uint8_t)len;
+      {
+        const uint32_t v = (code << (32 - len)) | len;
+        uint4* row = reinterpret_cast<uint4*>(&s_enc[32 * tid]);
+#pragma unroll
+        for (int k = 0; k < 8; k++) row[k] = make_uint4(v, v, v, v);
+      }
       cur_lut = lut;
       __syncthreads();
     }
@@ -270,10 +402,11 @@ encode_kernel(EncArgs A) {
 #pragma unroll
           for (int u = 0; u < kPass1Unroll; u++) q[u] = ldg_nc_v4(v + k + 32 * u);
 #pragma unroll
-          for (int u = 0; u < kPass1Unroll; u++) bits += len16(s_len, q[u]);
+          for (int u = 0; u < kPass1Unroll; u++) bits += entry_sum16(tab, q[u]);
         }
-        for (; k < nv; k += 32) bits += len16(s_len, ldg_nc_v4(v + k));
-        for (uint32_t t = nv * 16 + lane; t < m; t += 32) bits += s_len[in[cbeg + t]];
+        for (; k < nv; k += 32) bits += entry_sum16(tab, ldg_nc_v4(v + k));
+        for (uint32_t t = nv * 16 + lane; t < m; t += 32) bits += enc_entry(tab, in[cbeg + t]);
+        bits &= (1u << 21) - 1;  // a lane sums at most 4096 lengths of <= 11 bits
         bits = warp_sum_u32(bits);
         if (lane == 0) chunk_bits[g * kGroupChunks + c] = (uint16_t)bits;
       }
@@ -322,106 +455,47 @@ encode_kernel(EncArgs A) {
     for (uint32_t c = warp; c < kGroupChunks; c += kEncWarps) {
       const uint64_t cbeg = gbeg + (uint64_t)c * cs;
       if (cbeg >= gend) break;
-      const uint64_t cend = min(cbeg + cs, gend);
-      const uint32_t S = s_chunk_start[c], E = s_chunk_start[c + 1];
-      uint32_t base_bit = S;            // group-relative bit of this step's first symbol
-      uint32_t win = (S >> 5) & ~3u;    // group-relative word of stage word 4
-      int cur = 0;
-      uint4 qn = make_uint4(0, 0, 0, 0);
-      {
-        const uint64_t my = cbeg + (uint64_t)lane * 16;
-        if (my + 16 <= cend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + my));
+      const uint32_t m = (uint32_t)(min(cbeg + cs, gend) - cbeg);
+      const uint32_t S = s_chunk_start[c];
+      Packer pk;
+      pk.tab = tab;
+      pk.stage = &s_stage[warp][0][0];
+      pk.stage_s = stage_s;
+      pk.dst = dst;
+      pk.seam_s = (uint32_t)__cvta_generic_to_shared(&s_seam[c][0]);
+      pk.seam_idx_s = (uint32_t)__cvta_generic_to_shared(&s_seam_idx[c][0]);
+      pk.seam_blk = (S & 127u) ? (S >> 7) : ~0u;
+      pk.base_bit = S;
+      pk.win = (S >> 5) & ~3u;
+      pk.cur = 0;
+      pk.lane = lane;
+      // full steps, with the input of the next two steps in flight
+      const uint32_t n_full = m / kSub;
+      const uint4* src = reinterpret_cast<const uint4*>(in + cbeg) + lane;
+      uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
+      if (n_full > 0) q0 = ldg_nc_v4(src);
+      if (n_full > 1) q1 = ldg_nc_v4(src + 32);
+      for (uint32_t i = 0; i < n_full; i++) {
+        const uint4 q = q0;
+        q0 = q1;
+        if (i + 2 < n_full) q1 = ldg_nc_v4(src + 32 * (i + 2));
+        pk.step<false>(q, 16);
       }
-      for (uint64_t tbeg = cbeg; tbeg < cend; tbeg += kSub) {
-        const uint64_t my = tbeg + (uint64_t)lane * 16;
-        uint4 q = qn;
-        int cnt = 16;
-        if (my + 16 > cend) {  // ragged end of the last chunk only
-          cnt = my < cend ? (int)(cend - my) : 0;
-          uint32_t w[4] = {0, 0, 0, 0};
-          for (int j = 0; j < cnt; j++) w[j >> 2] |= (uint32_t)in[my + j] << (8 * (j & 3));
-          q = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        {
-          const uint64_t nx = my + kSub;
-          if (nx + 16 <= cend) qn = ldg_nc_v4(reinterpret_cast<const uint4*>(in + nx));
-        }
-        // 16 codewords -> 8 pairs: MSB-aligned (at most 22 bits), lengths in P/L8.
-        // An entry is codeword << (32 - len) | len, so e & 31 == len.
-        uint32_t P[8], L8[8];
-        uint32_t L = 0;
-        const uint32_t qw[4] = {q.x, q.y, q.z, q.w};
-        uint32_t e[16];
-        if (cnt == 16) {
+      // the ragged end of a tensor's last chunk: lane l takes symbols 16 l ...
+      if (m % kSub) {
+        const uint32_t off = n_full * kSub + 16u * lane;
+        const int cnt = off < m ? (int)min(16u, m - off) : 0;
+        uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
-          for (int j = 0; j < 16; j++) e[j] = s_enc[__byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3))];
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; j++) e[j] = j < cnt ? s_enc[__byte_perm(qw[j >> 2], 0, 0x4440 + (j & 3))] : 0u;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-          const uint32_t e0 = e[2 * k], e1 = e[2 * k + 1];
-          P[k] = (e0 & ~31u) | __funnelshift_r(e1 & ~31u, 0u, e0);  // second code right after the first
-          L8[k] = (e0 + e1) & 31u;  // the two lengths; code bits sit above bit 20
-          L += L8[k];
-        }
-        uint32_t incl = L;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += t;
-        }
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        // Place each pair (at most 22 bits: at most two words) at its bit
-        // position with two unconditional shared ORs; the second ORs 0 when
-        // the pair ends inside its first word.  Neighbouring pairs and lanes
-        // share words, hence OR.
-        {
-          uint32_t p = base_bit + incl - L + 32u * (4u - win);  // bit relative to stage word 0
-          const uint32_t sbase = stage_s + cur * kWStage * 4;
-#pragma unroll
-          for (int k = 0; k < 8; k++) {
-            const uint32_t r = p & 31u;
-            const uint32_t wa = sbase + (p >> 5) * 4;
-            red_or(wa, P[k] >> r);
-            red_or(wa + 4, __funnelshift_rc(0u, P[k], r));  // P << (32 - r), 0 when r == 0
-            p += L8[k];
-          }
-        }
-        __syncwarp();
-        // completed 16-byte blocks go out (the chunk's first block, when it is
-        // shared with the previous chunk, goes to the seam); the partial last
-        // block moves to the other buffer; what was read is zeroed for reuse
-        const uint32_t end_bit = base_bit + total;
-        const uint32_t nblk = ((end_bit >> 5) - win) / 4;
-        uint32_t* sb = &s_stage[warp][cur][4];
-        for (uint32_t b = lane; b < nblk; b += 32) {
-          uint4* s4 = reinterpret_cast<uint4*>(&sb[4 * b]);
-          const uint4 v = *s4;
-          const uint32_t blk = win / 4 + b;
-          const uint4 be = make_uint4(bswap32(v.x), bswap32(v.y), bswap32(v.z), bswap32(v.w));
-          if (blk == (S >> 7) && (S & 127u)) {
-            s_seam[c][0] = be;
-            s_seam_idx[c][0] = blk;
-          } else {
-            st_cs_v4(&dst[blk], be);
-          }
-          *s4 = make_uint4(0, 0, 0, 0);
-        }
-        if (lane < 4) {
-          s_stage[warp][cur ^ 1][4 + lane] = sb[4 * nblk + lane];
-          sb[4 * nblk + lane] = 0;
-        }
-        win += 4 * nblk;
-        base_bit = end_bit;
-        cur ^= 1;
-        __syncwarp();
+        for (int j = 0; j < 16; j++)
+          if (j < cnt) w[j >> 2] |= (uint32_t)in[cbeg + off + j] << (8 * (j & 3));
+        pk.step<true>(make_uint4(w[0], w[1], w[2], w[3]), cnt);
       }
       // the chunk's partial last block (shared with the next chunk, or the
       // group's zero-padded end) goes to the seam; the buffer is left zeroed
       if (lane == 0) {
-        uint32_t* cb = &s_stage[warp][cur][4];
+        const uint32_t E = s_chunk_start[c + 1];
+        uint32_t* cb = pk.stage + pk.cur * kWStage + 4;
         if (E & 127u) {
           s_seam[c][1] = make_uint4(bswap32(cb[0]), bswap32(cb[1]), bswap32(cb[2]), bswap32(cb[3]));
           s_seam_idx[c][1] = E >> 7;
