@@ -41,12 +41,18 @@ __device__ __forceinline__ void red_or(uint32_t saddr, uint32_t v) {
   asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
 }
 
-// OR v into a shared word when nb >= 32 (predicated, no branch).
-__device__ __forceinline__ void red_or_if_full(uint32_t saddr, uint32_t v, uint32_t nb) {
+// Store v to a shared word when nb >= 32 (a predicated store, no branch).
+__device__ __forceinline__ void st_shared_if_full(uint32_t saddr, uint32_t v, uint32_t nb) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ge.u32 q, %2, 32;\n\t@q red.shared.or.b32 [%0], %1;\n\t}" ::"r"(saddr),
+      "{\n\t.reg .pred q;\n\tsetp.ge.u32 q, %2, 32;\n\t@q st.shared.u32 [%0], %1;\n\t}" ::"r"(saddr),
       "r"(v), "r"(nb)
       : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t saddr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
@@ -247,20 +253,23 @@ struct Packer {
     }
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
     // Each lane packs its pairs into a two-word accumulator (hi:lo, hi
-    // first) that starts at the lane's bit offset within a word, and ORs each
-    // completed word into the stage.  Only a lane's first and last words can
-    // be shared with the neighbouring lanes, hence OR.
+    // first) that starts at the lane's bit offset within its first word,
+    // preloaded with that word (the bits carried from the previous step, in
+    // lane 0; zero elsewhere).  Every completed word is stored whole: a lane's
+    // first word also holds the previous lane's last bits, which that lane
+    // ORs in afterwards with its partial last word.  Stores precede the ORs
+    // in program order, and no two lanes store the same word.
     {
       const uint32_t p = base_bit + incl - L + 32u * (4u - win);  // bit relative to stage word 0
       uint32_t wa = stage_s + cur * kWStage * 4 + (p >> 5) * 4;
       uint32_t nb = p & 31u;  // bits in hi
-      uint32_t hi = 0;
+      uint32_t hi = ld_shared_u32(wa);
 #pragma unroll
       for (int k = 0; k < 8; k++) {
         hi |= P[k] >> nb;
         const uint32_t lo = __funnelshift_rc(0u, P[k], nb);  // P << (32 - nb), 0 when nb == 0
         nb += L8[k];                                         // at most 31 + 22
-        red_or_if_full(wa, hi, nb);
+        st_shared_if_full(wa, hi, nb);
         const uint32_t full = nb >> 5;
         hi = full ? lo : hi;
         wa += full * 4;
