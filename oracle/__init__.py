@@ -59,6 +59,14 @@ def lib() -> ctypes.CDLL:
         L.oracle_code_bits.restype = u64
         L.oracle_huffman_roundtrip.argtypes = [P, u64, P]
         L.oracle_huffman_roundtrip.restype = u64
+        L.oracle_e4m3_value.argtypes = [ctypes.c_uint8]
+        L.oracle_e4m3_value.restype = ctypes.c_double
+        L.oracle_e4m3_nearest.argtypes = [ctypes.c_float]
+        L.oracle_e4m3_nearest.restype = ctypes.c_uint8
+        L.oracle_quantize_block32.argtypes = [P, u64, P, P]
+        L.oracle_dequantize_block32.argtypes = [P, P, u64, P]
+        L.oracle_bf16_to_f32.argtypes = [P, u64, P]
+        L.oracle_f32_to_bf16.argtypes = [P, u64, P]
         _lib = L
     return _lib
 
@@ -198,3 +206,48 @@ def huffman_roundtrip(x, hist=None) -> int:
 def huffman_bits(hist) -> int:
     h = _hist(hist)
     return int((huffman_lengths(h).astype(np.uint64) * h).sum())
+
+
+def e4m3_value(c: int) -> float:
+    """Value of one e4m3 byte (Section 3, all-finite eXmY)."""
+    return float(lib().oracle_e4m3_value(int(c)))
+
+
+def e4m3_nearest(v: float) -> int:
+    """Nearest e4m3 byte to the fp32 value v (ties to the even code)."""
+    return int(lib().oracle_e4m3_nearest(float(v)))
+
+
+def bf16_to_f32(x) -> np.ndarray:
+    """uint16 bf16 bit patterns -> float32 (exact)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.uint16).reshape(-1))
+    out = np.zeros(x.size, np.float32)
+    lib().oracle_bf16_to_f32(_p(x), x.size, _p(out))
+    return out
+
+
+def f32_to_bf16(x) -> np.ndarray:
+    """float32 -> uint16 bf16 bit patterns, round to nearest even."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1))
+    out = np.zeros(x.size, np.uint16)
+    lib().oracle_f32_to_bf16(_p(x), x.size, _p(out))
+    return out
+
+
+def quantize_block32(x):
+    """(status, codes uint8[n], scales float32[ceil(n/32)]) of float32 x."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1))
+    codes = np.zeros(max(x.size, 1), np.uint8)
+    scales = np.zeros(max((x.size + 31) // 32, 1), np.float32)
+    st = lib().oracle_quantize_block32(_p(x), x.size, _p(codes), _p(scales))
+    return int(st), codes[: x.size].copy(), scales[: (x.size + 31) // 32].copy()
+
+
+def dequantize_block32(codes, scales) -> np.ndarray:
+    """float32 values of e4m3 codes with one scale per 32 elements."""
+    c = _u8(codes)
+    sc = np.ascontiguousarray(np.asarray(scales, dtype=np.float32).reshape(-1))
+    assert sc.size >= (c.size + 31) // 32
+    out = np.zeros(max(c.size, 1), np.float32)
+    lib().oracle_dequantize_block32(_p(c), _p(sc), c.size, _p(out))
+    return out[: c.size].copy()

@@ -15,6 +15,8 @@
  *     decoder reads the area code, then that area's suffix bits, adds the
  *     area's offset and looks the rank up in a 256-entry table (Table 4).
  *   - Section 4: entropy and compressibility = (8 - bits per symbol) / 8.
+ *   - Section 3: the tensors are e4m3 in the all-finite eXmY variant, with a
+ *     scale per block of 32 elements.
  *
  * Readings where the paper is silent or ambiguous:
  *   R1 Last area (8 suffix bits): Table 3 prints ranks 253..255 as
@@ -25,6 +27,12 @@
  *   R2 Equal counts: the smaller symbol value gets the smaller rank.
  *   R3 Bits are written most significant first; the first bit of a stream is
  *      bit 7 of its first byte.
+ *   R5 Block-32 quantisation (Section 3 names the format and block size
+ *      only): scale = absmax / 480 in fp32, code = the nearest e4m3 value to
+ *      x / scale (fp32 division), ties to the even code, saturating at 480,
+ *      sign kept; an all-zero block has scale 0 and codes 0x00.  The codec
+ *      itself never depends on this; only the fused quantise / dequantise
+ *      entry points and the input generator do.
  *   R4 Scheme family: areas with fewer than 8 suffix bits hold exactly
  *      2^bits ranks; areas with 8 suffix bits hold 1..256; the counts sum to
  *      256 and suffix widths never decrease from area to area.
@@ -489,4 +497,76 @@ uint64_t oracle_huffman_roundtrip(const uint8_t *x, uint64_t n,
   }
   free(buf);
   return rpos == total ? total : UINT64_MAX;
+}
+
+/* ---- Block-32 e4m3 quantisation (Section 3: eXmY e4m3, block size 32) ---- */
+
+double oracle_e4m3_value(uint8_t c) {
+  const int s = c >> 7, e = (c >> 3) & 15, m = c & 7;
+  const double mag = e == 0 ? m * ldexp(1.0, -9) : (1.0 + m / 8.0) * ldexp(1.0, e - 7);
+  return s ? -mag : mag;
+}
+
+uint8_t oracle_e4m3_nearest(float v) {
+  const double a = fabs((double)v); /* exact */
+  int best;
+  if (a >= 480.0) {
+    best = 127; /* nothing lies above 480: saturate */
+  } else {
+    /* lo = the largest magnitude code with value <= a; a lies in
+     * [value(lo), value(lo + 1)) and the nearer end wins, the even code on a
+     * tie.  The midpoint of two neighbours is exact in double. */
+    int lo = 0;
+    for (int c = 1; c < 128; c++)
+      if (oracle_e4m3_value((uint8_t)c) <= a) lo = c;
+    const double mid = (oracle_e4m3_value((uint8_t)lo) + oracle_e4m3_value((uint8_t)(lo + 1))) / 2;
+    if (a < mid)
+      best = lo;
+    else if (a > mid)
+      best = lo + 1;
+    else
+      best = (lo & 1) ? lo + 1 : lo;
+  }
+  return (uint8_t)(best | (signbit(v) ? 0x80 : 0));
+}
+
+int oracle_quantize_block32(const float *x, uint64_t n, uint8_t *codes, float *scales) {
+  int st = ORACLE_OK;
+  for (uint64_t b0 = 0; b0 < n; b0 += 32) {
+    const uint64_t b1 = b0 + 32 < n ? b0 + 32 : n;
+    float amax = 0.0f;
+    for (uint64_t i = b0; i < b1; i++) {
+      if (!isfinite(x[i])) st = ORACLE_ERR_ARG;
+      const float a = fabsf(x[i]);
+      if (a > amax) amax = a;
+    }
+    const float scale = amax / 480.0f;
+    scales[b0 / 32] = scale;
+    for (uint64_t i = b0; i < b1; i++) codes[i] = amax > 0.0f ? oracle_e4m3_nearest(x[i] / scale) : 0;
+  }
+  return st;
+}
+
+void oracle_dequantize_block32(const uint8_t *codes, const float *scales, uint64_t n, float *out) {
+  for (uint64_t i = 0; i < n; i++) out[i] = (float)oracle_e4m3_value(codes[i]) * scales[i / 32];
+}
+
+void oracle_bf16_to_f32(const uint16_t *x, uint64_t n, float *out) {
+  for (uint64_t i = 0; i < n; i++) {
+    const uint32_t u = (uint32_t)x[i] << 16;
+    memcpy(&out[i], &u, 4);
+  }
+}
+
+void oracle_f32_to_bf16(const float *x, uint64_t n, uint16_t *out) {
+  for (uint64_t i = 0; i < n; i++) {
+    /* the two bf16 neighbours of x[i] and the one nearer (ties: even) */
+    uint32_t u;
+    memcpy(&u, &x[i], 4);
+    const uint32_t lo = u & 0xFFFF0000u, hi = lo + 0x10000u;
+    const uint32_t rest = u & 0xFFFFu;
+    uint32_t pick = lo;
+    if (rest > 0x8000u || (rest == 0x8000u && ((lo >> 16) & 1u))) pick = hi;
+    out[i] = (uint16_t)(pick >> 16);
+  }
 }

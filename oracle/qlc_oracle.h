@@ -83,6 +83,34 @@ uint64_t oracle_code_bits(const uint64_t hist[256], const uint16_t area_n[8],
 uint64_t oracle_huffman_roundtrip(const uint8_t *x, uint64_t n,
                                   const uint64_t hist[256]);
 
+/* ---- Block-32 e4m3 quantisation (Section 3) -- the f4 fusion's oracle ----
+ * e4m3 here is the all-finite eXmY format: sign = bit 7, exponent = bits
+ * 6..3 with bias 7, mantissa = bits 2..0; exponent 0 is subnormal
+ * (m * 2^-9), otherwise (1 + m/8) * 2^(e-7); the largest value is 480. */
+
+/* Value of an e4m3 byte. */
+double oracle_e4m3_value(uint8_t c);
+
+/* The e4m3 byte nearest to v (ties: the even code): |v| is placed between
+ * two neighbouring magnitudes by scanning all 128 and compared with their
+ * midpoint; values of 480 and beyond give 480; the sign of v is kept (so -0
+ * and tiny negatives give 0x80). */
+uint8_t oracle_e4m3_nearest(float v);
+
+/* Blocks of 32 consecutive elements (the last may be shorter): scale =
+ * absmax / 480 in fp32, code = nearest(x / scale) with the division in fp32;
+ * a block whose absmax is 0 gets scale 0 and codes 0x00.  Returns
+ * ORACLE_ERR_ARG if any element is not finite. */
+int oracle_quantize_block32(const float *x, uint64_t n, uint8_t *codes, float *scales);
+
+/* out[i] = float(value(codes[i])) * scales[i / 32], the product in fp32. */
+void oracle_dequantize_block32(const uint8_t *codes, const float *scales, uint64_t n, float *out);
+
+/* bf16 <-> fp32: widening is exact; narrowing rounds to nearest, ties to
+ * the even bf16 (finite values only). */
+void oracle_bf16_to_f32(const uint16_t *x, uint64_t n, float *out);
+void oracle_f32_to_bf16(const float *x, uint64_t n, uint16_t *out);
+
 #ifdef __cplusplus
 }
 #endif
