@@ -245,6 +245,45 @@ qlc_status qlc_decode_batch(const qlc_desc *d_descs, int n_shards, void *d_ws, s
 qlc_status qlc_peek_header(const void *h_hdr, size_t hdr_bytes, uint64_t *n,
                            uint64_t *container_bytes);
 
+/* ---- Block-32 e4m3 quantisation fused with the codec (Section 3) ----
+ * The paper's tensors are e4m3 (the all-finite eXmY variant) with one scale
+ * per block of 32 consecutive elements.  These calls fuse that quantisation
+ * into the pass that counts the histogram (Section 4), and the
+ * dequantisation into the decoder's output (Section 7), so the e4m3 codes
+ * make one trip less through HBM on each side.
+ * Rule per block (the last block may be shorter): scale = absmax / 480 in
+ * fp32; code = the e4m3 byte nearest to x / scale (fp32 division), ties to
+ * the even code, saturating at 480, sign kept; a block whose scale is 0
+ * (absmax 0, or absmax / 480 rounding to 0) gets codes 0x00.
+ * Value of a code: sign * m 2^-9 for exponent field 0, else
+ * sign * (1 + m/8) 2^(e-7). */
+typedef enum { QLC_DTYPE_F32 = 0, QLC_DTYPE_BF16 = 1 } qlc_dtype;
+
+/* Quantises n elements of d_x (dtype) into e4m3 codes d_codes[n] and scales
+ * d_scales[ceil(n/32)] (fp32), and, when d_hist is not NULL, counts the codes
+ * into d_hist[256] (added when accumulate != 0, else overwritten) in the same
+ * pass, ready for qlc_build_lut.  d_x, d_codes and d_scales 16-byte aligned.
+ * A non-finite element sets *d_status to QLC_ERR_ARG (its block's codes are
+ * then unspecified).  Async on stream. */
+qlc_status qlc_quantize_e4m3(const void *d_x, qlc_dtype dtype, size_t n, uint8_t *d_codes,
+                             float *d_scales, uint64_t *d_hist, int accumulate,
+                             uint32_t *d_status, qlc_stream_t stream);
+
+/* d_out[i] = value(d_codes[i]) * d_scales[i / 32] with the product in fp32
+ * (for QLC_DTYPE_BF16 then rounded to nearest even).  d_codes and d_out
+ * 16-byte aligned.  Async on stream. */
+qlc_status qlc_dequantize_e4m3(const uint8_t *d_codes, const float *d_scales, size_t n,
+                               void *d_out, qlc_dtype dtype, qlc_stream_t stream);
+
+/* qlc_decode and qlc_dequantize_e4m3 in one pass: each chunk's decoded codes
+ * become values (d_scales: one per 32 symbols of the tensor) before they
+ * leave the chip.  d_out: out_cap elements of dtype, 16-byte aligned;
+ * *d_n_out receives n.  Validation and errors as qlc_decode (out_cap counts
+ * elements).  Async on stream. */
+qlc_status qlc_decode_dequantize(const uint8_t *d_in, size_t in_bytes, const float *d_scales,
+                                 void *d_out, qlc_dtype dtype, size_t out_cap, uint64_t *d_n_out,
+                                 uint32_t *d_status, qlc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@
  *   R5 Block-32 quantisation (Section 3 names the format and block size
  *      only): scale = absmax / 480 in fp32, code = the nearest e4m3 value to
  *      x / scale (fp32 division), ties to the even code, saturating at 480,
- *      sign kept; an all-zero block has scale 0 and codes 0x00.  The codec
+ *      sign kept; a block whose scale is 0 (absmax 0, or absmax / 480 below
+ *      the smallest fp32 subnormal) has codes 0x00.  The codec
  *      itself never depends on this; only the fused quantise / dequantise
  *      entry points and the input generator do.
  *   R4 Scheme family: areas with fewer than 8 suffix bits hold exactly
@@ -542,7 +543,7 @@ int oracle_quantize_block32(const float *x, uint64_t n, uint8_t *codes, float *s
     }
     const float scale = amax / 480.0f;
     scales[b0 / 32] = scale;
-    for (uint64_t i = b0; i < b1; i++) codes[i] = amax > 0.0f ? oracle_e4m3_nearest(x[i] / scale) : 0;
+    for (uint64_t i = b0; i < b1; i++) codes[i] = scale > 0.0f ? oracle_e4m3_nearest(x[i] / scale) : 0;
   }
   return st;
 }

@@ -99,7 +99,8 @@ uint8_t oracle_e4m3_nearest(float v);
 
 /* Blocks of 32 consecutive elements (the last may be shorter): scale =
  * absmax / 480 in fp32, code = nearest(x / scale) with the division in fp32;
- * a block whose absmax is 0 gets scale 0 and codes 0x00.  Returns
+ * a block whose scale is 0 (absmax 0, or absmax / 480 rounding to 0) gets
+ * codes 0x00.  Returns
  * ORACLE_ERR_ARG if any element is not finite. */
 int oracle_quantize_block32(const float *x, uint64_t n, uint8_t *codes, float *scales);
 

@@ -15,6 +15,8 @@
 // predication, so lanes never diverge.  Output: 16 symbols per shared store
 // into a swizzled 32 x 32-byte tile; every 32 symbols the warp writes the tile
 // out, one 32-byte segment per chunk.
+#include <cuda_bf16.h>
+
 #include "qlc_common.cuh"
 
 namespace qlc {
@@ -222,9 +224,65 @@ __device__ void build_table(const uint8_t* in, DecShared& sm, int lane) {
   __syncwarp();
 }
 
+// Output of the decoder: the symbols themselves (kOutCodes), or their
+// block-32 dequantised values (value(code) * scale, fp32 or rounded to bf16).
+constexpr int kOutCodes = -1;
+
+// Sixteen decoded symbols v of one chunk, starting at symbol index i of the
+// tensor (a multiple of 16), to their destination.
+template <int kOut>
+__device__ __forceinline__ void put16(void* out, const float* scales, uint64_t i, uint4 v) {
+  if (kOut == kOutCodes) {
+    // streaming store: the output is written once
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(static_cast<uint8_t*>(out) + i), "r"(v.x),
+                 "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+  } else {
+    const float sc = scales[i / 32];
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    float y[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) y[j] = e4m3_to_f32((w[j >> 2] >> (8 * (j & 3))) & 0xFFu) * sc;
+    if (kOut == QLC_DTYPE_F32) {
+      float4* o = reinterpret_cast<float4*>(static_cast<float*>(out) + i);
+#pragma unroll
+      for (int k = 0; k < 4; k++) __stcs(o + k, make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]));
+    } else {
+      uint32_t p[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
+        p[k] = *reinterpret_cast<const uint32_t*>(&hb);
+      }
+      uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + i);
+      __stcs(o, make_uint4(p[0], p[1], p[2], p[3]));
+      __stcs(o + 1, make_uint4(p[4], p[5], p[6], p[7]));
+    }
+  }
+}
+
+// Fewer than 16 symbols (a tensor's ragged end).
+template <int kOut>
+__device__ __forceinline__ void put_tail(void* out, const float* scales, uint64_t i, const uint8_t* sb,
+                                         uint32_t cnt) {
+  for (uint32_t b = 0; b < cnt; b++) {
+    if (kOut == kOutCodes) {
+      static_cast<uint8_t*>(out)[i + b] = sb[b];
+    } else {
+      const float y = e4m3_to_f32(sb[b]) * scales[(i + b) / 32];
+      if (kOut == QLC_DTYPE_F32)
+        static_cast<float*>(out)[i + b] = y;
+      else
+        static_cast<__nv_bfloat16*>(out)[i + b] = __float2bfloat16_rn(y);
+    }
+  }
+}
+
 // Decodes group g of a validated container (one warp; lane = chunk).
-__device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
-                             uint64_t g, DecShared& sm, LaneDec& d, uint32_t* status, int lane) {
+template <int kOut>
+__device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in, void* __restrict__ out,
+                             const float* __restrict__ scales, uint64_t g, DecShared& sm, LaneDec& d,
+                             uint32_t* status, int lane) {
   const unsigned long long* group_off = reinterpret_cast<const unsigned long long*>(in + kIndexOff);
   const uint16_t* chunk_bits = reinterpret_cast<const uint16_t*>(in + kIndexOff + 8 * h.n_groups);
   const uint4* vbase = reinterpret_cast<const uint4*>(in + h.P);
@@ -312,16 +370,10 @@ __device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in,
         const uint32_t off = i0 + 16 * q;
         if (off < rn) {
           const uint4* src = &s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
-          uint8_t* dst = out + rc * cs + off;
-          if (off + 16 <= rn) {
-            const uint4 v = *src;  // streaming store: the output is written once
-            asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(dst), "r"(v.x), "r"(v.y), "r"(v.z),
-                         "r"(v.w)
-                         : "memory");
-          } else {
-            const uint8_t* sb = reinterpret_cast<const uint8_t*>(src);
-            for (uint32_t b = 0; b < rn - off; b++) dst[b] = sb[b];
-          }
+          if (off + 16 <= rn)
+            put16<kOut>(out, scales, rc * cs + off, *src);
+          else
+            put_tail<kOut>(out, scales, rc * cs + off, reinterpret_cast<const uint8_t*>(src), rn - off);
         }
       }
       __syncwarp();
@@ -337,9 +389,11 @@ __device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in,
 
 // One container: every CTA (one warp) validates the header, builds its table
 // and decodes groups blockIdx.x, blockIdx.x + gridDim.x, ...
+template <int kOut>
 __global__ void __launch_bounds__(32, kDecCtasPerSm)
-decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __restrict__ out,
-              uint64_t out_cap, unsigned long long* __restrict__ n_out, uint32_t* __restrict__ status) {
+decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, void* __restrict__ out,
+              const float* __restrict__ scales, uint64_t out_cap, unsigned long long* __restrict__ n_out,
+              uint32_t* __restrict__ status) {
   __shared__ DecShared sm;
   const int lane = threadIdx.x;
   DecHeader h;
@@ -360,7 +414,8 @@ decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, uint8_t* __rest
   build_table(in, sm, lane);
   LaneDec d;
   d.ring_s = (uint32_t)__cvta_generic_to_shared(&sm.ring[lane * kRingVec]);
-  for (uint64_t g = blockIdx.x; g < h.n_groups; g += gridDim.x) decode_group(h, in, out, g, sm, d, status, lane);
+  for (uint64_t g = blockIdx.x; g < h.n_groups; g += gridDim.x)
+    decode_group<kOut>(h, in, out, scales, g, sm, d, status, lane);
 }
 
 // A batch: warps take (shard, group) items from a device counter; a warp
@@ -413,7 +468,7 @@ decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
       cur = sh;
     }
     if (g == 0 && lane == 0 && dd.out_bytes) *dd.out_bytes = h.n;
-    if (g < h.n_groups) decode_group(h, in, static_cast<uint8_t*>(dd.out), g, sm, d, status, lane);
+    if (g < h.n_groups) decode_group<kOutCodes>(h, in, dd.out, nullptr, g, sm, d, status, lane);
   }
 }
 
@@ -421,16 +476,37 @@ decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
 
 using namespace qlc;
 
+static int decode_grid(uint64_t out_cap) {
+  const uint64_t max_groups = (out_cap + kGroupChunks * QLC_MIN_CHUNK - 1) / (kGroupChunks * QLC_MIN_CHUNK);
+  const uint64_t cap = (uint64_t)sm_count() * kDecCtasPerSm;
+  return (int)(max_groups < 1 ? 1 : (max_groups < cap ? max_groups : cap));
+}
+
 extern "C" qlc_status qlc_decode(const uint8_t* d_in, size_t in_bytes, uint8_t* d_out, size_t out_cap,
                                  uint64_t* d_n_out, uint32_t* d_status, qlc_stream_t stream) {
   if (!d_in || !d_n_out || (out_cap > 0 && !d_out)) return QLC_ERR_ARG;
   if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0)
     return QLC_ERR_ARG;
-  const uint64_t max_groups = (out_cap + kGroupChunks * QLC_MIN_CHUNK - 1) / (kGroupChunks * QLC_MIN_CHUNK);
-  const uint64_t cap = (uint64_t)sm_count() * kDecCtasPerSm;
-  const int grid = (int)(max_groups < 1 ? 1 : (max_groups < cap ? max_groups : cap));
-  decode_kernel<<<grid, 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
-      d_in, in_bytes, d_out, out_cap, reinterpret_cast<unsigned long long*>(d_n_out), d_status);
+  decode_kernel<kOutCodes><<<decode_grid(out_cap), 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+      d_in, in_bytes, d_out, nullptr, out_cap, reinterpret_cast<unsigned long long*>(d_n_out), d_status);
+  return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
+}
+
+extern "C" qlc_status qlc_decode_dequantize(const uint8_t* d_in, size_t in_bytes, const float* d_scales,
+                                            void* d_out, qlc_dtype dtype, size_t out_cap, uint64_t* d_n_out,
+                                            uint32_t* d_status, qlc_stream_t stream) {
+  if (dtype != QLC_DTYPE_F32 && dtype != QLC_DTYPE_BF16) return QLC_ERR_ARG;
+  if (!d_in || !d_n_out || (out_cap > 0 && (!d_out || !d_scales))) return QLC_ERR_ARG;
+  if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0)
+    return QLC_ERR_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned long long* no = reinterpret_cast<unsigned long long*>(d_n_out);
+  if (dtype == QLC_DTYPE_F32)
+    decode_kernel<QLC_DTYPE_F32><<<decode_grid(out_cap), 32, 0, st>>>(d_in, in_bytes, d_out, d_scales, out_cap, no,
+                                                                     d_status);
+  else
+    decode_kernel<QLC_DTYPE_BF16><<<decode_grid(out_cap), 32, 0, st>>>(d_in, in_bytes, d_out, d_scales, out_cap,
+                                                                      no, d_status);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
 

@@ -73,6 +73,14 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// The value of an e4m3 byte (Section 3, all-finite eXmY): its sign and
+// magnitude bits placed at fp32 bits 31 and 26..20 read as (1 + m/8) 2^(e-127)
+// for e >= 1 and m 2^-129 for e = 0 (an fp32 subnormal); one exact
+// multiplication by 2^120 gives the value.
+__device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
+  return __uint_as_float(((c & 0x80u) << 24) | ((c & 0x7Fu) << 20)) * 0x1p120f;
+}
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

@@ -83,9 +83,13 @@ def _load() -> ctypes.CDLL:
     L.qlc_build_lut_batch.argtypes = [P, i32, P, i32, P, P]
     L.qlc_encode_batch.argtypes = [P, i32, u32, P, sz, P, P, P]
     L.qlc_decode_batch.argtypes = [P, i32, P, sz, P, P, P]
+    L.qlc_quantize_e4m3.argtypes = [P, i32, sz, P, P, P, i32, P, P]
+    L.qlc_dequantize_e4m3.argtypes = [P, P, sz, P, i32, P]
+    L.qlc_decode_dequantize.argtypes = [P, sz, P, P, i32, sz, P, P, P]
     for f in ("qlc_scheme_table", "qlc_histogram", "qlc_build_lut", "qlc_build_lut_host",
               "qlc_build_lut_best", "qlc_encode", "qlc_decode", "qlc_peek_header", "qlc_encode_noalloc",
-              "qlc_histogram_batch", "qlc_build_lut_batch", "qlc_encode_batch", "qlc_decode_batch"):
+              "qlc_histogram_batch", "qlc_build_lut_batch", "qlc_encode_batch", "qlc_decode_batch",
+              "qlc_quantize_e4m3", "qlc_dequantize_e4m3", "qlc_decode_dequantize"):
         getattr(L, f).restype = i32
     return L
 
@@ -222,6 +226,46 @@ def qlc_decode(d_in: torch.Tensor, d_out: torch.Tensor, d_n_out: torch.Tensor, d
     out_cap = _nbytes(d_out) if out_cap is None else out_cap
     _check(lib.qlc_decode(_ptr(d_in), in_bytes, _ptr(d_out), out_cap, _ptr(d_n_out), _ptr(d_status),
                           _stream(stream)), "qlc_decode")
+
+
+DTYPE_F32, DTYPE_BF16 = 0, 1
+
+
+def _dtype_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return DTYPE_F32
+    if t.dtype == torch.bfloat16:
+        return DTYPE_BF16
+    raise QlcError(ERR_ARG, f"dtype {t.dtype} (float32 or bfloat16)")
+
+
+def qlc_quantize_e4m3(d_x: torch.Tensor, d_codes: torch.Tensor, d_scales: torch.Tensor,
+                      d_hist: torch.Tensor | None, d_status: torch.Tensor, accumulate: bool = False,
+                      n: int | None = None, stream=None) -> None:
+    """d_x: CUDA float32 or bfloat16; d_codes: uint8[n]; d_scales: float32[ceil(n/32)];
+    d_hist: int64[256] or None."""
+    n = d_x.numel() if n is None else n
+    _check(lib.qlc_quantize_e4m3(_ptr(d_x), _dtype_of(d_x), n, _ptr(d_codes), _ptr(d_scales),
+                                 _ptr(d_hist) if d_hist is not None else None, int(bool(accumulate)),
+                                 _ptr(d_status), _stream(stream)), "qlc_quantize_e4m3")
+
+
+def qlc_dequantize_e4m3(d_codes: torch.Tensor, d_scales: torch.Tensor, d_out: torch.Tensor,
+                        n: int | None = None, stream=None) -> None:
+    """d_out: CUDA float32 or bfloat16 with at least n elements."""
+    n = d_codes.numel() if n is None else n
+    _check(lib.qlc_dequantize_e4m3(_ptr(d_codes), _ptr(d_scales), n, _ptr(d_out), _dtype_of(d_out),
+                                   _stream(stream)), "qlc_dequantize_e4m3")
+
+
+def qlc_decode_dequantize(d_in: torch.Tensor, d_scales: torch.Tensor, d_out: torch.Tensor,
+                          d_n_out: torch.Tensor, d_status: torch.Tensor, in_bytes: int | None = None,
+                          stream=None) -> None:
+    """Decode a container straight to float32 / bfloat16 values (d_out's dtype)."""
+    in_bytes = _nbytes(d_in) if in_bytes is None else in_bytes
+    _check(lib.qlc_decode_dequantize(_ptr(d_in), in_bytes, _ptr(d_scales), _ptr(d_out), _dtype_of(d_out),
+                                     d_out.numel(), _ptr(d_n_out), _ptr(d_status), _stream(stream)),
+           "qlc_decode_dequantize")
 
 
 def qlc_peek_header(hdr: bytes):

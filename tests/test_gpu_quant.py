@@ -1,0 +1,188 @@
+"""GPU parity of the fused block-32 e4m3 entry points (Section 3) against the
+oracle: quantisation with the histogram counted in the same pass, plain
+dequantisation, and decoding straight to values.  Codes, scales, histogram
+counts and every output value (compared as bit patterns) must match exactly:
+the oracle takes the same fp32 decisions (scale = absmax / 480, x / scale,
+value * scale) as the kernels."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2602_17849_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qlc():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2602_17849_gb300 import _build
+    _build.build()
+    from paper_2602_17849_gb300 import qlc as q
+    return q
+
+
+def _floats(n, seed):
+    g = torch.Generator().manual_seed(seed)
+    x = torch.randn(n, generator=g) * torch.exp(torch.randn(n, generator=g) * 2)
+    if n >= 96:
+        x[:32] = 0.0                                          # an all-zero block
+        x[32:64] = -0.0 * x[32:64]                            # negative zeros and values
+        x[40] = -0.0
+        x[64:96] = torch.tensor(1e-44) * torch.arange(32)     # scale rounds to 0
+    if n >= 160:
+        x[96:128] = torch.tensor(2.0 ** -140)                 # subnormal scale
+        x[128:160] = torch.tensor([2.0 ** -10, -(2.0 ** -10), 7.5, 480.0] * 8)  # ties, extremes
+    return x
+
+
+def _gpu_quantize(qlc, x):
+    n = x.numel()
+    xd = x.cuda()
+    codes = torch.empty(max(n, 16), dtype=torch.uint8, device="cuda")
+    scales = torch.empty(max((n + 31) // 32, 4), dtype=torch.float32, device="cuda")
+    hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    qlc.qlc_quantize_e4m3(xd, codes, scales, hist, st)
+    torch.cuda.synchronize()
+    return (int(st.item()), codes[:n].cpu().numpy(), scales[: (n + 31) // 32].cpu().numpy(),
+            hist.cpu().numpy().astype(np.uint64))
+
+
+def _as_f32_host(x: torch.Tensor) -> np.ndarray:
+    if x.dtype == torch.bfloat16:
+        return oracle.bf16_to_f32(x.view(torch.int16).numpy().view(np.uint16))
+    return x.numpy()
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 127, 128, 129, 255, 257, 1000, 32 * 4096 + 17, 1 << 20])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_quantize_matches_oracle(qlc, n, dtype):
+    x = _floats(n, seed=n).to(dtype)
+    st, codes, scales, hist = _gpu_quantize(qlc, x)
+    ost, ocodes, oscales = oracle.quantize_block32(_as_f32_host(x))
+    assert st == ost == 0
+    assert np.array_equal(codes, ocodes)
+    assert np.array_equal(scales.view(np.uint32), oscales.view(np.uint32))
+    assert np.array_equal(hist, oracle.histogram(ocodes))
+
+
+def test_quantize_non_finite_is_an_argument_error(qlc):
+    for bad in (float("nan"), float("inf"), float("-inf")):
+        x = _floats(4096, seed=2)
+        x[1234] = bad
+        st, _, _, _ = _gpu_quantize(qlc, x)
+        ost, _, _ = oracle.quantize_block32(x.numpy())
+        assert st == ost == oracle.ERR_ARG
+
+
+@pytest.mark.parametrize("n", [1, 17, 32, 1000, 32 * 4096 + 17])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_dequantize_matches_oracle(qlc, n, dtype):
+    rng = np.random.default_rng(n)
+    codes = rng.integers(0, 256, n, dtype=np.uint8)
+    scales = (rng.standard_normal((n + 31) // 32) ** 2 * 0.01).astype(np.float32)
+    scales[0] = 0.0
+    out = torch.empty(max(n, 16), dtype=dtype, device="cuda")
+    qlc.qlc_dequantize_e4m3(torch.from_numpy(codes).cuda(), torch.from_numpy(scales).cuda(), out, n=n)
+    torch.cuda.synchronize()
+    want = oracle.dequantize_block32(codes, scales)
+    got = out[:n].cpu()
+    if dtype == torch.bfloat16:
+        assert np.array_equal(got.view(torch.int16).numpy().view(np.uint16), oracle.f32_to_bf16(want))
+    else:
+        assert np.array_equal(got.numpy().view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("n,cs", [(1, 128), (4097, 1024), (32 * 4096 + 333, 4096), (3 * (1 << 20) + 5, 4096)])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_fused_pipeline_matches_oracle(qlc, n, cs, dtype):
+    """x -> quantise + histogram -> LUT -> encode -> decode straight to values:
+    the container is the oracle's container of the oracle's codes, and the
+    values are the oracle's dequantised codes, bit for bit."""
+    x = _floats(n, seed=100 + n).to(dtype)
+    xd = x.cuda()
+    codec = qlc.Codec(max(n, 1), cs, 1)
+    codes = torch.empty(max(n, 16), dtype=torch.uint8, device="cuda")
+    scales = torch.empty(max((n + 31) // 32, 4), dtype=torch.float32, device="cuda")
+    qlc.qlc_quantize_e4m3(xd, codes, scales, codec.hist, codec.status)
+    qlc.qlc_build_lut(codec.hist, 1, codec.lut)
+    cont = codec.new_container()
+    codec.encode_into(codes[:n], cont, build_lut=False)
+    torch.cuda.synchronize()
+    codec.check()
+    nbytes = int(codec.out_bytes.item())
+    y = torch.empty(max(n, 16), dtype=dtype, device="cuda")
+    qlc.qlc_decode_dequantize(cont, scales, y, codec.n_out, codec.status, in_bytes=nbytes)
+    torch.cuda.synchronize()
+    codec.check()
+    assert int(codec.n_out.item()) == n
+    ost, ocodes, oscales = oracle.quantize_block32(_as_f32_host(x))
+    assert ost == 0
+    want_c = oracle.encode(ocodes, scheme_id=1, chunk_symbols=cs)
+    assert np.array_equal(cont[:nbytes].cpu().numpy(), want_c)
+    dst, dcodes, _ = oracle.decode(want_c)
+    assert dst == 0
+    want = oracle.dequantize_block32(dcodes, oscales)
+    got = y[:n].cpu()
+    if dtype == torch.bfloat16:
+        assert np.array_equal(got.view(torch.int16).numpy().view(np.uint16), oracle.f32_to_bf16(want))
+    else:
+        assert np.array_equal(got.numpy().view(np.uint32), want.view(np.uint32))
+
+
+def test_decode_dequantize_corrupt_and_capacity(qlc):
+    x = inputs.make_e4m3("t4", 50_000, seed=4)
+    c = oracle.encode(x.numpy(), scheme_id=1, chunk_symbols=1024)
+    scales = torch.ones(2000, dtype=torch.float32, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    small = torch.empty(49_999, dtype=torch.float32, device="cuda")
+    qlc.qlc_decode_dequantize(torch.from_numpy(c).cuda(), scales, small, n_out, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == qlc.ERR_CAPACITY and int(n_out.item()) == 50_000
+    bad = c.copy()
+    bad[400] ^= 0x5A                                      # chunk_bits[0]
+    st.zero_()
+    y = torch.empty(50_000, dtype=torch.float32, device="cuda")
+    qlc.qlc_decode_dequantize(torch.from_numpy(bad).cuda(), scales, y, n_out, st)
+    torch.cuda.synchronize()
+    ost, _, _ = oracle.decode(bad)
+    assert int(st.item()) == ost == oracle.ERR_CORRUPT
+
+
+def test_full_size_fused_sampled(qlc):
+    """64 Mi fp32 elements (256 MiB): the device histogram equals the oracle's
+    histogram of the device codes; 2048 sampled blocks match the oracle's
+    quantisation; decoding straight to values equals plain dequantisation of
+    the codes, and sampled values match the oracle."""
+    n = 64 << 20
+    g = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.randn(n, generator=g, device="cuda") * torch.exp(torch.randn(n, generator=g, device="cuda"))
+    codes = torch.empty(n, dtype=torch.uint8, device="cuda")
+    scales = torch.empty(n // 32, dtype=torch.float32, device="cuda")
+    codec = qlc.Codec(n, 4096, 1)
+    qlc.qlc_quantize_e4m3(x, codes, scales, codec.hist, codec.status)
+    qlc.qlc_build_lut(codec.hist, 1, codec.lut)
+    cont = codec.new_container()
+    codec.encode_into(codes, cont, build_lut=False)
+    y = torch.empty(n, dtype=torch.float32, device="cuda")
+    qlc.qlc_decode_dequantize(cont, scales, y, codec.n_out, codec.status, in_bytes=None)
+    ref = torch.empty(n, dtype=torch.float32, device="cuda")
+    qlc.qlc_dequantize_e4m3(codes, scales, ref)
+    torch.cuda.synchronize()
+    codec.check()
+    assert torch.equal(y.view(torch.int32), ref.view(torch.int32))
+    ch = codes.cpu().numpy()
+    assert np.array_equal(codec.hist.cpu().numpy().astype(np.uint64), oracle.histogram(ch))
+    rng = np.random.default_rng(8)
+    blocks = rng.choice(n // 32, 2048, replace=False)
+    xs = x.view(-1, 32)[torch.from_numpy(blocks).cuda()].cpu().numpy().reshape(-1)
+    ost, oc, osc = oracle.quantize_block32(xs)
+    assert ost == 0
+    assert np.array_equal(ch.reshape(-1, 32)[blocks].reshape(-1), oc)
+    assert np.array_equal(scales.cpu().numpy()[blocks].view(np.uint32), osc.view(np.uint32))
+    want = oracle.dequantize_block32(oc, osc)
+    got = y.view(-1, 32)[torch.from_numpy(blocks).cuda()].cpu().numpy().reshape(-1)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))

@@ -1,9 +1,10 @@
 """Pins of the oracle's block-32 e4m3 quantisation (Section 3: eXmY e4m3 with
 a scale per block of 32), the reference for the fused quantise / dequantise
 entry points.  The oracle places |v| between two neighbouring magnitudes by
-scanning all 128 and compares it with their midpoint; it is checked here against the format's defining values, exact
-ties, saturation, an independent frexp-based quantiser (the input generator's,
-in PyTorch), the rounding error bound, and PyTorch's own bf16 conversion."""
+scanning all 128 and compares it with their midpoint.  It is checked against
+the format's defining values, exact ties, saturation, an independent
+frexp-based quantiser (the input generator's, in PyTorch), the rounding error
+bound, and PyTorch's own bf16 conversion."""
 import numpy as np
 import torch
 
@@ -96,6 +97,15 @@ def test_quantise_error_bound_and_absmax():
     cb = codes.reshape(-1, 32)
     am = np.argmax(np.abs(xb), axis=1)
     assert np.all(cb[np.arange(cb.shape[0]), am] & 0x7F == 0x7F)
+
+
+def test_scale_underflow_gives_zero_codes():
+    x = np.zeros(64, np.float32)
+    x[:32] = np.float32(1e-44) * np.arange(32, dtype=np.float32)   # absmax / 480 rounds to 0
+    x[32:] = np.float32(2.0 ** -140)                               # subnormal scale, ratio 512
+    st, codes, scales = oracle.quantize_block32(x)
+    assert st == 0 and scales[0] == 0 and np.all(codes[:32] == 0)
+    assert scales[1] > 0 and np.all(codes[32:] == 0x7F)
 
 
 def test_non_finite_input_is_an_argument_error():
