@@ -279,6 +279,78 @@ def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152)
     }
 
 
+def fused_leg(dev, steps: int, warmup: int, peak: float):
+    """Block-32 e4m3 quantisation fused into the codec: a [16384 x 16384] fp32
+    Student-t(4) activation tensor (the values the headline tensor quantises),
+    encoded as quantise + histogram -> LUT -> encode and decoded straight to
+    fp32, against the same work with a separate histogram pass and a separate
+    dequantisation pass.  Every output is checked bit-exact against the
+    unfused path."""
+    import torch
+
+    from paper_2602_17849_gb300 import inputs, qlc
+    n = N_BYTES
+    x = inputs.make_f32("t4", n, seed=0, device=dev)
+    torch.cuda.empty_cache()
+    codes = torch.empty(n, dtype=torch.uint8, device=dev)
+    scales = torch.empty(n // 32, dtype=torch.float32, device=dev)
+    codec = qlc.Codec(n, CHUNK, SCHEME, dev)
+    cont = codec.new_container()
+    y = torch.empty(n, dtype=torch.float32, device=dev)
+    y2 = torch.empty(n, dtype=torch.float32, device=dev)
+    codes2 = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def enc_fused():
+        qlc.qlc_quantize_e4m3(x, codes, scales, codec.hist, codec.status, stream=stream)
+        qlc.qlc_build_lut(codec.hist, SCHEME, codec.lut, stream=stream)
+        qlc.qlc_encode(codes, codec.lut, CHUNK, cont, codec.ws, codec.out_bytes, codec.status, stream=stream)
+
+    def enc_plain():
+        qlc.qlc_quantize_e4m3(x, codes, scales, None, codec.status, stream=stream)
+        qlc.qlc_histogram(codes, codec.hist, stream=stream)
+        qlc.qlc_build_lut(codec.hist, SCHEME, codec.lut, stream=stream)
+        qlc.qlc_encode(codes, codec.lut, CHUNK, cont, codec.ws, codec.out_bytes, codec.status, stream=stream)
+
+    def dec_fused():
+        qlc.qlc_decode_dequantize(cont, scales, y, codec.n_out, codec.status, stream=stream)
+
+    def dec_plain():
+        qlc.qlc_decode(cont, codes2, codec.n_out, codec.status, stream=stream)
+        qlc.qlc_dequantize_e4m3(codes2, scales, y2, stream=stream)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    t_ef, t_ep, t_df, t_dp = timed(enc_fused), timed(enc_plain), timed(dec_fused), timed(dec_plain)
+    codec.check()
+    c_bytes = int(codec.out_bytes.item())
+    assert torch.equal(y.view(torch.int32), y2.view(torch.int32)) and torch.equal(codes, codes2)
+    # quantise + histogram alone, for its roofline
+    t_q = timed(lambda: qlc.qlc_quantize_e4m3(x, codes, scales, codec.hist, codec.status, stream=stream))
+    q_bytes = 4 * n + n + n // 8
+    d_bytes = c_bytes + n // 8 + 4 * n
+    return {
+        "workload": "[16384 x 16384] fp32 Student-t(4) activations, block-32 e4m3, chunk 4096, Table 1",
+        "encode_fused_ms": t_ef, "encode_unfused_ms": t_ep, "decode_fused_ms": t_df, "decode_unfused_ms": t_dp,
+        "encode_fused_gbs_fp32": 4 * n / (t_ef * 1e-3) / 1e9, "decode_fused_gbs_fp32": 4 * n / (t_df * 1e-3) / 1e9,
+        "speedup_encode": t_ep / t_ef, "speedup_decode": t_dp / t_df,
+        "quantize_hist_ms": t_q, "quantize_hist_roofline_frac": q_bytes / (t_q * 1e-3) / 1e9 / peak,
+        "decode_dequantize_roofline_frac": d_bytes / (t_df * 1e-3) / 1e9 / peak,
+        "bytes_counted": "quantise+hist: 4N read + N codes + N/8 scales written; decode->fp32: C + N/8 read, 4N written",
+        "bit_exact_vs_unfused": True,
+    }
+
+
 def serve_leg(dev, seconds: float):
     """Serving: Poisson arrivals at 20,000 requests/s, half compress and half
     decompress, sizes log-uniform 4 KiB - 64 MiB of Student-t e4m3 data
@@ -316,6 +388,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-batched", action="store_true", help="skip the 1152-shard batched leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg length (0 = skip)")
+    ap.add_argument("--no-fused", action="store_true", help="skip the fused quantise / dequantise leg")
     ap.add_argument("--batched-shards", type=int, default=1152,
                     help="shards in the batched leg (fewer only for profiling captures)")
     args = ap.parse_args()
@@ -473,6 +546,8 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.batched_shards)
+    if not args.no_fused:
+        line["fused_quantize"] = fused_leg(dev, max(3, args.steps // 2), args.warmup, peak)
     if args.serve_seconds > 0:
         line["serving"] = serve_leg(dev, args.serve_seconds)
     if rank == 0 and world == 1 and args.cpu_budget > 0:

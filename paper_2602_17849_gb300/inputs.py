@@ -143,6 +143,23 @@ def make_e4m3(kind: str, n: int, seed: int, device="cpu", piece: int = 1 << 26) 
     return out
 
 
+def make_f32(kind: str, n: int, seed: int, device="cpu", piece: int = 1 << 26) -> torch.Tensor:
+    """The fp32 values that make_e4m3 quantises (same kinds, seeds and pieces
+    of draws), for the fused quantise entry points: quantize_block32 of this
+    tensor equals make_e4m3(kind, n, seed, device)."""
+    device = torch.device(device)
+    if kind in ("uniform_bytes", "constant") or kind not in KINDS:
+        raise ValueError(kind)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    out = torch.empty(n, dtype=torch.float32, device=device)
+    piece = max(BLOCK, piece - piece % BLOCK)
+    for s in range(0, n, piece):
+        m = min(piece, n - s)
+        out[s:s + m] = _draw(kind, m, gen, device)
+    return out
+
+
 def cfg3_shards(n_shards: int = 1152, lo: int = 64 << 10, hi: int = 16 << 20, base_seed: int = 1000):
     """Shard sizes and kinds of the batched workload: sizes log-uniform in
     [lo, hi] rounded to a multiple of 128, drawn with seed base_seed + i;

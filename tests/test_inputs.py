@@ -76,3 +76,9 @@ def test_cfg3_shard_sizes():
     assert min(sizes) >= 64 << 10 and max(sizes) <= 16 << 20
     assert 2.5e9 < sum(sizes) < 4.5e9
     assert kinds[:3] == ["t4", "gauss", "laplace"] and seeds[0] == 1000
+
+
+def test_make_f32_is_what_make_e4m3_quantises():
+    for kind in ("t4", "gauss", "laplace_outliers", "ffn2"):
+        x = inputs.make_f32(kind, 70_001, seed=5, piece=1 << 15)
+        assert torch.equal(inputs.quantize_block32(x), inputs.make_e4m3(kind, 70_001, seed=5, piece=1 << 15))
