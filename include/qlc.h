@@ -37,9 +37,13 @@
  *     only the device can see, a wait that timed out) are written to
  *     *d_status with an atomic compare-and-swap from 0, so the first error
  *     is kept: set *d_status to 0 before a sequence of calls and read it after.
- *   - Device input and output buffers of qlc_histogram, qlc_encode and
- *     qlc_decode must be 16-byte aligned (cudaMalloc and PyTorch allocations
- *     are); otherwise QLC_ERR_ARG.
+ *   - Device pointers must be aligned (cudaMalloc and PyTorch allocations
+ *     are): byte buffers (inputs, outputs, containers, workspaces, value
+ *     arrays), qlc_lut and qlc_desc arrays to 16 bytes; histograms and
+ *     64-bit results (d_out_bytes, d_n_out) to 8; status words and scales to
+ *     4.  A misaligned pointer returns QLC_ERR_ARG before anything is
+ *     launched; in a batch, a descriptor with a misaligned pointer sets
+ *     *d_status to QLC_ERR_ARG and its shard is skipped.
  */
 #ifndef QLC_H
 #define QLC_H

@@ -37,8 +37,8 @@ __device__ uint64_t item_count(int kind, const qlc_desc& d, uint32_t cs, uint32_
   if (kind == kPlanEncode) {
     const uint64_t n = d.in_bytes;
     const uint64_t n_chunks = (n + cs - 1) / cs;
-    if (!d.out || !d.lut || !al16(d.out) || (n > 0 && (!d.in || !al16(d.in))) ||
-        n_chunks > 0xFFFFFFFFull) {
+    if (!d.out || !d.lut || !al16(d.out) || !al16(d.lut) || !aligned(d.out_bytes, 8) ||
+        (n > 0 && (!d.in || !al16(d.in))) || n_chunks > 0xFFFFFFFFull) {
       set_status(status, QLC_ERR_ARG);
       return 0;
     }
@@ -49,7 +49,7 @@ __device__ uint64_t item_count(int kind, const qlc_desc& d, uint32_t cs, uint32_
     return n == 0 ? 1 : n_groups_of(n_chunks);
   }
   // decode: the container's groups, from a header that at least parses
-  if (!d.in || !al16(d.in) || (d.out_cap > 0 && (!d.out || !al16(d.out)))) {
+  if (!d.in || !al16(d.in) || !aligned(d.out_bytes, 8) || (d.out_cap > 0 && (!d.out || !al16(d.out)))) {
     set_status(status, QLC_ERR_ARG);
     return 0;
   }
@@ -198,7 +198,7 @@ size_t qlc_batch_workspace_size(int n_shards, uint64_t total_symbols, uint32_t c
 qlc_status qlc_histogram_batch(const qlc_desc* d_descs, int n_shards, uint64_t* d_hists, int shared,
                                void* d_ws, size_t ws_bytes, qlc_stream_t stream) {
   if (!d_descs || n_shards < 1 || !d_hists || !d_ws) return QLC_ERR_ARG;
-  if ((reinterpret_cast<uintptr_t>(d_ws) & 15u) != 0) return QLC_ERR_ARG;
+  if (!aligned(d_ws, 16) || !aligned(d_descs, 16) || !aligned(d_hists, 8)) return QLC_ERR_ARG;
   BatchWs w;
   if (!batch_ws_layout(d_ws, ws_bytes, n_shards, &w)) return QLC_ERR_CAPACITY;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

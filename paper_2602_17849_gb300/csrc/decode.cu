@@ -485,7 +485,7 @@ static int decode_grid(uint64_t out_cap) {
 extern "C" qlc_status qlc_decode(const uint8_t* d_in, size_t in_bytes, uint8_t* d_out, size_t out_cap,
                                  uint64_t* d_n_out, uint32_t* d_status, qlc_stream_t stream) {
   if (!d_in || !d_n_out || (out_cap > 0 && !d_out)) return QLC_ERR_ARG;
-  if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0)
+  if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_n_out, 8) || !aligned(d_status, 4))
     return QLC_ERR_ARG;
   decode_kernel<kOutCodes><<<decode_grid(out_cap), 32, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       d_in, in_bytes, d_out, nullptr, out_cap, reinterpret_cast<unsigned long long*>(d_n_out), d_status);
@@ -497,7 +497,8 @@ extern "C" qlc_status qlc_decode_dequantize(const uint8_t* d_in, size_t in_bytes
                                             uint32_t* d_status, qlc_stream_t stream) {
   if (dtype != QLC_DTYPE_F32 && dtype != QLC_DTYPE_BF16) return QLC_ERR_ARG;
   if (!d_in || !d_n_out || (out_cap > 0 && (!d_out || !d_scales))) return QLC_ERR_ARG;
-  if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0)
+  if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_scales, 4) || !aligned(d_n_out, 8) ||
+      !aligned(d_status, 4))
     return QLC_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   unsigned long long* no = reinterpret_cast<unsigned long long*>(d_n_out);
@@ -513,7 +514,7 @@ extern "C" qlc_status qlc_decode_dequantize(const uint8_t* d_in, size_t in_bytes
 extern "C" qlc_status qlc_decode_batch(const qlc_desc* d_descs, int n_shards, void* d_ws, size_t ws_bytes,
                                        uint32_t* d_status, const qlc_launch* h_launch, qlc_stream_t stream) {
   if (!d_descs || n_shards < 1 || !d_ws) return QLC_ERR_ARG;
-  if ((reinterpret_cast<uintptr_t>(d_ws) & 15u) != 0) return QLC_ERR_ARG;
+  if (!aligned(d_ws, 16) || !aligned(d_descs, 16) || !aligned(d_status, 4)) return QLC_ERR_ARG;
   BatchWs w;
   if (!batch_ws_layout(d_ws, ws_bytes, n_shards, &w)) return QLC_ERR_CAPACITY;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -587,7 +587,8 @@ qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint3
                       uint64_t* d_out_bytes, uint32_t* d_status, qlc_stream_t stream) {
   if (!d_lut || !d_out || !d_out_bytes || (n > 0 && (!d_in || !d_ws))) return QLC_ERR_ARG;
   if (!chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
-  if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0)
+  if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_lut, 16) || !aligned(d_ws, 16) ||
+      !aligned(d_out_bytes, 8) || !aligned(d_status, 4))
     return QLC_ERR_ARG;
   const uint64_t n_chunks = (n + chunk_symbols - 1) / chunk_symbols;
   if (n_chunks > 0xFFFFFFFFull) return QLC_ERR_ARG;
@@ -621,7 +622,8 @@ qlc_status qlc_test_encode_stalled_lookback(const uint8_t* d_in, size_t n, const
                                             void* d_ws, size_t ws_bytes, uint64_t* d_out_bytes,
                                             uint32_t* d_status, qlc_stream_t stream) {
   if (!d_in || !d_lut || !d_out || !d_ws || !chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
-  if (((reinterpret_cast<uintptr_t>(d_in) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0)
+  if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_lut, 16) || !aligned(d_ws, 16) ||
+      !aligned(d_out_bytes, 8) || !aligned(d_status, 4))
     return QLC_ERR_ARG;
   const uint64_t n_chunks = (n + chunk_symbols - 1) / chunk_symbols;
   if (n_groups_of(n_chunks) < 2) return QLC_ERR_ARG;
@@ -650,7 +652,7 @@ qlc_status qlc_encode_batch(const qlc_desc* d_descs, int n_shards, uint32_t chun
                             size_t ws_bytes, uint32_t* d_status, const qlc_launch* h_launch,
                             qlc_stream_t stream) {
   if (!d_descs || n_shards < 1 || !d_ws || !chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
-  if ((reinterpret_cast<uintptr_t>(d_ws) & 15u) != 0) return QLC_ERR_ARG;
+  if (!aligned(d_ws, 16) || !aligned(d_descs, 16) || !aligned(d_status, 4)) return QLC_ERR_ARG;
   BatchWs w;
   if (!batch_ws_layout(d_ws, ws_bytes, n_shards, &w)) return QLC_ERR_CAPACITY;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -208,7 +208,7 @@ int qlc_scheme_check(const qlc_scheme* s) { return scheme_valid(s) ? 1 : 0; }
 qlc_status qlc_histogram(const uint8_t* d_in, size_t n, uint64_t* d_hist, int accumulate,
                          qlc_stream_t stream) {
   if (!d_hist || (n > 0 && !d_in)) return QLC_ERR_ARG;
-  if ((reinterpret_cast<uintptr_t>(d_in) & 15u) != 0) return QLC_ERR_ARG;
+  if (!aligned(d_in, 16) || !aligned(d_hist, 8)) return QLC_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (!accumulate && cudaMemsetAsync(d_hist, 0, 256 * sizeof(uint64_t), st) != cudaSuccess)
     return QLC_ERR_CUDA;
@@ -224,6 +224,7 @@ qlc_status qlc_histogram(const uint8_t* d_in, size_t n, uint64_t* d_hist, int ac
 qlc_status qlc_build_lut(const uint64_t* d_hist, const qlc_scheme* h_scheme, qlc_lut* d_lut,
                          qlc_stream_t stream) {
   if (!d_hist || !d_lut || !scheme_valid(h_scheme)) return QLC_ERR_ARG;
+  if (!aligned(d_hist, 8) || !aligned(d_lut, 16)) return QLC_ERR_ARG;
   lut_kernel<<<1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const unsigned long long*>(d_hist), clean_scheme(h_scheme), d_lut);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
@@ -232,6 +233,7 @@ qlc_status qlc_build_lut(const uint64_t* d_hist, const qlc_scheme* h_scheme, qlc
 qlc_status qlc_build_lut_best(const uint64_t* d_hist, const qlc_scheme* h_schemes, int n_schemes,
                               qlc_lut* d_lut, qlc_stream_t stream) {
   if (!d_hist || !d_lut || !h_schemes || n_schemes < 1 || n_schemes > 8) return QLC_ERR_ARG;
+  if (!aligned(d_hist, 8) || !aligned(d_lut, 16)) return QLC_ERR_ARG;
   SchemeSet set;
   set.count = n_schemes;
   for (int k = 0; k < n_schemes; k++) {
@@ -247,6 +249,7 @@ qlc_status qlc_build_lut_batch(const uint64_t* d_hists, int n_luts, const qlc_sc
                                int n_schemes, qlc_lut* d_luts, qlc_stream_t stream) {
   if (!d_hists || !d_luts || !h_schemes || n_luts < 1 || n_schemes < 1 || n_schemes > 8)
     return QLC_ERR_ARG;
+  if (!aligned(d_hists, 8) || !aligned(d_luts, 16)) return QLC_ERR_ARG;
   SchemeSet set;
   set.count = n_schemes;
   for (int k = 0; k < n_schemes; k++) {

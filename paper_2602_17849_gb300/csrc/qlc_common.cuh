@@ -42,6 +42,12 @@ __host__ __device__ inline bool scheme_ok(const uint16_t n[8], const uint8_t b[8
   return total == 256;
 }
 
+// Alignment of a caller's pointer to a bytes (a power of two); NULL counts as
+// aligned, the entry points check NULL where it matters.
+__host__ __device__ __forceinline__ bool aligned(const void* p, uintptr_t a) {
+  return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0;
+}
+
 // First error wins.
 __device__ __forceinline__ void set_status(uint32_t* st, uint32_t code) {
   if (st) atomicCAS(st, 0u, code);

@@ -215,8 +215,8 @@ extern "C" qlc_status qlc_quantize_e4m3(const void* d_x, qlc_dtype dtype, size_t
                                         qlc_stream_t stream) {
   if (dtype != QLC_DTYPE_F32 && dtype != QLC_DTYPE_BF16) return QLC_ERR_ARG;
   if (n > 0 && (!d_x || !d_codes || !d_scales)) return QLC_ERR_ARG;
-  if (((reinterpret_cast<uintptr_t>(d_x) | reinterpret_cast<uintptr_t>(d_codes) |
-        reinterpret_cast<uintptr_t>(d_scales)) & 15u) != 0)
+  if (!aligned(d_x, 16) || !aligned(d_codes, 16) || !aligned(d_scales, 16) || !aligned(d_hist, 8) ||
+      !aligned(d_status, 4))
     return QLC_ERR_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (d_hist && !accumulate && cudaMemsetAsync(d_hist, 0, 256 * sizeof(uint64_t), st) != cudaSuccess)
@@ -238,7 +238,7 @@ extern "C" qlc_status qlc_dequantize_e4m3(const uint8_t* d_codes, const float* d
                                           qlc_dtype dtype, qlc_stream_t stream) {
   if (dtype != QLC_DTYPE_F32 && dtype != QLC_DTYPE_BF16) return QLC_ERR_ARG;
   if (n > 0 && (!d_codes || !d_scales || !d_out)) return QLC_ERR_ARG;
-  if (((reinterpret_cast<uintptr_t>(d_codes) | reinterpret_cast<uintptr_t>(d_out)) & 15u) != 0) return QLC_ERR_ARG;
+  if (!aligned(d_codes, 16) || !aligned(d_out, 16) || !aligned(d_scales, 4)) return QLC_ERR_ARG;
   if (n == 0) return QLC_OK;
   const uint64_t want = ((n + 15) / 16 + 255) / 256;
   const uint64_t cap = (uint64_t)sm_count() * 8;
