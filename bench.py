@@ -279,7 +279,7 @@ def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152)
     }
 
 
-def fused_leg(dev, steps: int, warmup: int, peak: float):
+def fused_leg(dev, steps: int, warmup: int, peak: float, n: int = N_BYTES):
     """Block-32 e4m3 quantisation fused into the codec: a [16384 x 16384] fp32
     Student-t(4) activation tensor (the values the headline tensor quantises),
     encoded as quantise + histogram -> LUT -> encode and decoded straight to
@@ -289,11 +289,10 @@ def fused_leg(dev, steps: int, warmup: int, peak: float):
     import torch
 
     from paper_2602_17849_gb300 import inputs, qlc
-    n = N_BYTES
     x = inputs.make_f32("t4", n, seed=0, device=dev)
     torch.cuda.empty_cache()
     codes = torch.empty(n, dtype=torch.uint8, device=dev)
-    scales = torch.empty(n // 32, dtype=torch.float32, device=dev)
+    scales = torch.empty((n + 31) // 32, dtype=torch.float32, device=dev)
     codec = qlc.Codec(n, CHUNK, SCHEME, dev)
     cont = codec.new_container()
     y = torch.empty(n, dtype=torch.float32, device=dev)
@@ -340,7 +339,7 @@ def fused_leg(dev, steps: int, warmup: int, peak: float):
     q_bytes = 4 * n + n + n // 8
     d_bytes = c_bytes + n // 8 + 4 * n
     return {
-        "workload": "[16384 x 16384] fp32 Student-t(4) activations, block-32 e4m3, chunk 4096, Table 1",
+        "workload": f"{n} fp32 Student-t(4) activations, block-32 e4m3, chunk 4096, Table 1",
         "encode_fused_ms": t_ef, "encode_unfused_ms": t_ep, "decode_fused_ms": t_df, "decode_unfused_ms": t_dp,
         "encode_fused_gbs_fp32": 4 * n / (t_ef * 1e-3) / 1e9, "decode_fused_gbs_fp32": 4 * n / (t_df * 1e-3) / 1e9,
         "speedup_encode": t_ep / t_ef, "speedup_decode": t_dp / t_df,
@@ -389,6 +388,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 1152-shard batched leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg length (0 = skip)")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused quantise / dequantise leg")
+    ap.add_argument("--fused-elems", type=int, default=N_BYTES,
+                    help="elements in the fused leg (fewer only for profiling captures)")
     ap.add_argument("--batched-shards", type=int, default=1152,
                     help="shards in the batched leg (fewer only for profiling captures)")
     args = ap.parse_args()
@@ -547,7 +548,7 @@ def main():
     if not args.no_batched:
         line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.batched_shards)
     if not args.no_fused:
-        line["fused_quantize"] = fused_leg(dev, max(3, args.steps // 2), args.warmup, peak)
+        line["fused_quantize"] = fused_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.fused_elems)
     if args.serve_seconds > 0:
         line["serving"] = serve_leg(dev, args.serve_seconds)
     if rank == 0 and world == 1 and args.cpu_budget > 0:

@@ -108,6 +108,7 @@ plan_kernel(int kind, const qlc_desc* descs, int n_shards, uint32_t cs, BatchWs 
 // ------------------------------------------------------------- histograms
 
 constexpr int kHbWarps = 8;
+constexpr int kHbUnroll = 4;
 
 __device__ __forceinline__ void count16_batch(uint32_t* h, uint4 q) {
   const uint32_t w[4] = {q.x, q.y, q.z, q.w};
@@ -168,7 +169,15 @@ hist_batch_kernel(const qlc_desc* descs, int n_shards, const unsigned long long*
     const uint64_t end = min(beg + kHistItem, d.in_bytes);
     const uint4* v = reinterpret_cast<const uint4*>(in + beg);
     const uint64_t nvec = (end - beg) / 16;
-    for (uint64_t i = tid; i < nvec; i += blockDim.x) count16_batch(my, ldg_nc_v4(v + i));
+    uint64_t i = tid;
+    for (; i + (kHbUnroll - 1) * blockDim.x < nvec; i += kHbUnroll * blockDim.x) {
+      uint4 q[kHbUnroll];  // kHbUnroll loads in flight per thread
+#pragma unroll
+      for (int u = 0; u < kHbUnroll; u++) q[u] = ldg_nc_v4(v + i + u * blockDim.x);
+#pragma unroll
+      for (int u = 0; u < kHbUnroll; u++) count16_batch(my, q[u]);
+    }
+    for (; i < nvec; i += blockDim.x) count16_batch(my, ldg_nc_v4(v + i));
     for (uint64_t i = beg + nvec * 16 + tid; i < end; i += blockDim.x) {
       const uint32_t b = in[i];
       atomicAdd(&my[b + (b >> 7)], 1u);
