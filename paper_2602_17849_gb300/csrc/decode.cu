@@ -329,6 +329,18 @@ __device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in,
       d.nb1 = 63u - o;
     }
 
+    // the two 16-symbol pieces of each block this lane writes out: piece q of
+    // rows r = lane / 2 and 16 + lane / 2 (their chunks' lengths and first
+    // symbol indices are fixed for the group)
+    const int q = lane & 1;
+    uint32_t row_n[2];
+    uint64_t row_i[2];
+#pragma unroll
+    for (int t = 0; t < 2; t++) {
+      const uint64_t rc = g * kGroupChunks + 16 * t + (lane >> 1);
+      row_n[t] = rc < h.n_chunks ? (uint32_t)min((uint64_t)cs, h.n - rc * cs) : 0u;
+      row_i[t] = rc * cs + 16 * q;
+    }
     const uint32_t nmax = __reduce_max_sync(0xffffffffu, nsym);
     for (uint32_t i0 = 0; i0 < nmax; i0 += kBlk) {
       d.fetch();
@@ -364,16 +376,14 @@ __device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in,
       // the tile's row r is lane r's 32 output bytes: two 16-byte pieces per row
 #pragma unroll
       for (int t = 0; t < 2; t++) {
-        const int r = 16 * t + (lane >> 1), q = lane & 1;
-        const uint64_t rc = g * kGroupChunks + r;
-        const uint32_t rn = rc < h.n_chunks ? (uint32_t)min((uint64_t)cs, h.n - rc * cs) : 0u;
+        const int r = 16 * t + (lane >> 1);
         const uint32_t off = i0 + 16 * q;
-        if (off < rn) {
+        if (off < row_n[t]) {
           const uint4* src = &s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
-          if (off + 16 <= rn)
-            put16<kOut>(out, scales, rc * cs + off, *src);
+          if (off + 16 <= row_n[t])
+            put16<kOut>(out, scales, row_i[t] + i0, *src);
           else
-            put_tail<kOut>(out, scales, rc * cs + off, reinterpret_cast<const uint8_t*>(src), rn - off);
+            put_tail<kOut>(out, scales, row_i[t] + i0, reinterpret_cast<const uint8_t*>(src), row_n[t] - off);
         }
       }
       __syncwarp();
