@@ -153,8 +153,10 @@ size_t qlc_encode_workspace_size(size_t n, uint32_t chunk_symbols);
  * [128, 4096].  out_cap >= qlc_encoded_size(n, chunk_symbols), else
  * QLC_ERR_CAPACITY.  d_ws: ws_bytes >= qlc_encode_workspace_size() of device
  * scratch, overwritten (not preserved between calls).  *d_out_bytes receives
- * the container size.  Device errors (a look-back wait that exceeded its
- * time bound) go to *d_status.  Async on stream; d_in, d_out 16-byte aligned. */
+ * the container size.  Device errors go to *d_status: QLC_ERR_TIMEOUT when a
+ * look-back wait exceeded its time bound, QLC_ERR_ARG when a LUT entry is not
+ * a codeword of 3..11 bits (a LUT not made by qlc_build_lut*).  Async on
+ * stream; d_in, d_out 16-byte aligned. */
 qlc_status qlc_encode(const uint8_t *d_in, size_t n, const qlc_lut *d_lut,
                       uint32_t chunk_symbols, uint8_t *d_out, size_t out_cap,
                       void *d_ws, size_t ws_bytes, uint64_t *d_out_bytes,

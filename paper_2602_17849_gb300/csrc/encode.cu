@@ -1,14 +1,20 @@
 // encode.cu -- QLC encoder (Sections 5 and 7) writing container v1.
 //
-// One persistent kernel.  CTAs take groups (32 chunks) in ticket order:
-//   pass 1  each warp sums the code lengths of its chunks -> chunk_bits;
-//   look-back  the group publishes its padded byte size and finds the sum of
-//           all earlier groups' sizes (decoupled look-back, bounded waits);
-//   pass 2  the group's symbols are re-read (from L2: at most three groups
-//           per SM are in flight) and packed, 4096 symbols per tile: block scan of
-//           per-thread bit counts, MSB-first packing of each thread's 16
-//           codewords into a shared staging window, coalesced 16-byte stores
-//           of every completed 16-byte block.
+// One persistent kernel.  CTAs take groups (32 chunks) in ticket order; the
+// LUT is staged in shared memory once per tensor, one copy per lane, so every
+// lookup is free of bank conflicts.
+//   pass 1  each warp sums the code lengths of its chunks (w, w+8, ...) ->
+//           chunk_bits;
+//   look-back  warp 0 scans the 32 chunk sizes, publishes the group's padded
+//           byte size and finds the sum of all earlier groups' sizes
+//           (decoupled look-back, bounded waits);
+//   pass 2  each warp re-reads its chunks (from L2: at most three groups per
+//           SM are in flight) and packs them, 512 symbols per step: codeword
+//           pairs, a warp scan of the lanes' bit counts, per-lane word
+//           accumulation into a per-warp staging window (completed words are
+//           plain stores, a lane's partial last word one shared OR), and
+//           16-byte streaming stores of every completed 16-byte block; blocks
+//           shared by neighbouring chunks are merged once per group.
 // HBM traffic is one read of the input and one write of the container.
 #include "qlc_common.cuh"
 #include "../../include/qlc_testing.h"
