@@ -151,6 +151,24 @@ struct LaneDec {
     for (; fv < want; fv++) cp_async16(ring_s + (fv % kRingVec) * 16, gp + fv);
     cp_async_commit();
   }
+  // The same top-up between blocks, as three predicated copies with no
+  // branch: a block of kBlk symbols consumes at most kBlk * 11 bits = 44
+  // bytes, so the read position, and with it `want`, moves by at most three
+  // 16-byte vectors per block.
+  __device__ __forceinline__ void fetch3() {
+    const uint32_t want = min((rpb >> 4) + kRingVec, vend);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const uint32_t p = fv < want;
+      asm volatile(
+          "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q cp.async.cg.shared.global [%0], [%1], 16;\n\t}" ::"r"(
+              ring_s + (fv % kRingVec) * 16),
+          "l"(gp + fv), "r"(p)
+          : "memory");
+      fv += p;
+    }
+    cp_async_commit();
+  }
   __device__ __forceinline__ uint32_t ring_word(uint32_t byte_off) const {
     // ring_s is 128-byte aligned, so OR places the offset inside the ring
     return bswap32(ld_shared_u32(ring_s | (byte_off & (kRingVec * 16 - 1))));
@@ -227,6 +245,14 @@ __device__ void build_table(const uint8_t* in, DecShared& sm, int lane) {
 // Output of the decoder: the symbols themselves (kOutCodes), or their
 // block-32 dequantised values (value(code) * scale, fp32 or rounded to bf16).
 constexpr int kOutCodes = -1;
+
+// Streaming 16-byte store of decoded symbols when pred (a predicated store).
+__device__ __forceinline__ void put16_if(uint8_t* dst, uint4 v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};\n\t}" ::"l"(dst),
+      "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"((uint32_t)pred)
+      : "memory");
+}
 
 // Sixteen decoded symbols v of one chunk, starting at symbol index i of the
 // tensor (a multiple of 16), to their destination.
@@ -343,7 +369,7 @@ __device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in,
     }
     const uint32_t nmax = __reduce_max_sync(0xffffffffu, nsym);
     for (uint32_t i0 = 0; i0 < nmax; i0 += kBlk) {
-      d.fetch();
+      d.fetch3();
       cp_async_wait<1>();
       const uint32_t cnt = nsym > i0 ? min(kBlk, nsym - i0) : 0u;
       if (cnt == kBlk) {
@@ -374,16 +400,27 @@ __device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in,
       }
       __syncwarp();
       // the tile's row r is lane r's 32 output bytes: two 16-byte pieces per row
+      const bool ragged = __any_sync(0xffffffffu, i0 + kBlk > row_n[0] || i0 + kBlk > row_n[1]);
+      if (kOut == kOutCodes && !ragged) {
+        // every piece is whole: predicated streaming stores, no branch
 #pragma unroll
-      for (int t = 0; t < 2; t++) {
-        const int r = 16 * t + (lane >> 1);
-        const uint32_t off = i0 + 16 * q;
-        if (off < row_n[t]) {
-          const uint4* src = &s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
-          if (off + 16 <= row_n[t])
-            put16<kOut>(out, scales, row_i[t] + i0, *src);
-          else
-            put_tail<kOut>(out, scales, row_i[t] + i0, reinterpret_cast<const uint8_t*>(src), row_n[t] - off);
+        for (int t = 0; t < 2; t++) {
+          const int r = 16 * t + (lane >> 1);
+          const uint4 v = s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
+          put16_if(static_cast<uint8_t*>(out) + row_i[t] + i0, v, i0 + 16 * q < row_n[t]);
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < 2; t++) {
+          const int r = 16 * t + (lane >> 1);
+          const uint32_t off = i0 + 16 * q;
+          if (off < row_n[t]) {
+            const uint4* src = &s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
+            if (off + 16 <= row_n[t])
+              put16<kOut>(out, scales, row_i[t] + i0, *src);
+            else
+              put_tail<kOut>(out, scales, row_i[t] + i0, reinterpret_cast<const uint8_t*>(src), row_n[t] - off);
+          }
         }
       }
       __syncwarp();
