@@ -47,11 +47,20 @@ __device__ __forceinline__ void red_or(uint32_t saddr, uint32_t v) {
   asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
 }
 
-// Store v to a shared word when nb >= 32 (a predicated store, no branch).
-__device__ __forceinline__ void st_shared_if_full(uint32_t saddr, uint32_t v, uint32_t nb) {
+// When the accumulator's first word is complete (nb >= 32): store it to the
+// shared word at wa, move the spill word lo up, advance wa and nb by one word.
+// One predicate drives all of it, with no branch.
+__device__ __forceinline__ void emit_if_full(uint32_t& hi, uint32_t& wa, uint32_t& nb, uint32_t lo) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ge.u32 q, %2, 32;\n\t@q st.shared.u32 [%0], %1;\n\t}" ::"r"(saddr),
-      "r"(v), "r"(nb)
+      "{\n\t.reg .pred q;\n\t"
+      "setp.ge.u32 q, %2, 32;\n\t"
+      "@q st.shared.u32 [%1], %0;\n\t"
+      "selp.b32 %0, %3, %0, q;\n\t"
+      "@q add.u32 %1, %1, 4;\n\t"
+      "@q sub.u32 %2, %2, 32;\n\t"
+      "}"
+      : "+r"(hi), "+r"(wa), "+r"(nb)
+      : "r"(lo)
       : "memory");
 }
 
@@ -275,11 +284,7 @@ struct Packer {
         hi |= P[k] >> nb;
         const uint32_t lo = __funnelshift_rc(0u, P[k], nb);  // P << (32 - nb), 0 when nb == 0
         nb += L8[k];                                         // at most 31 + 22
-        st_shared_if_full(wa, hi, nb);
-        const uint32_t full = nb >> 5;
-        hi = full ? lo : hi;
-        wa += full * 4;
-        nb &= 31u;
+        emit_if_full(hi, wa, nb, lo);
       }
       red_or(wa, hi);  // the partial last word (0 adds nothing)
     }
