@@ -6,7 +6,7 @@
 // 32 chunks) with a block-wide prefix sum; the persistent kernels then take
 // items from a device counter, so shards of very different sizes share the
 // GPU evenly and no host round trip is needed.
-#include "qlc_common.cuh"
+#include "hist_cols.cuh"
 
 namespace qlc {
 
@@ -107,36 +107,27 @@ plan_kernel(int kind, const qlc_desc* descs, int n_shards, uint32_t cs, BatchWs 
 
 // ------------------------------------------------------------- histograms
 
-constexpr int kHbWarps = 8;
-constexpr int kHbUnroll = 4;
-
-__device__ __forceinline__ void count16_batch(uint32_t* h, uint4 q) {
-  const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-  for (int k = 0; k < 4; k++)
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      const uint32_t b = (w[k] >> (8 * j)) & 0xFFu;
-      atomicAdd(&h[b + (b >> 7)], 1u);
-    }
-}
-
-// Each CTA takes a contiguous run of items (so consecutive items usually
-// belong to the same shard) and flushes its shared histogram only when the
-// target histogram changes.
-__global__ void __launch_bounds__(kHbWarps * 32)
+// Each CTA (seven warps, lane-private columns from hist_cols.cuh; two CTAs
+// per SM over the launch, one resident at a time) takes a contiguous run of
+// items.  Its items of one shard are one
+// contiguous byte range, counted in a single streaming pass; the columns are
+// flushed into a shard's histogram when the target histogram changes (never,
+// for one shared histogram).  A CTA's run is at most one item per SM's share
+// of the batch, under 2^32 bytes per shard as long as the batch holds fewer
+// than 2^32 x SMs bytes.
+__global__ void __launch_bounds__(kHcThreads, 1)
 hist_batch_kernel(const qlc_desc* descs, int n_shards, const unsigned long long* item_base,
                   unsigned long long* hists, int shared) {
-  __shared__ uint32_t sh[kHbWarps][257];
-  const int tid = threadIdx.x;
+  extern __shared__ __align__(16) uint32_t hc_sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned long long total = item_base[n_shards];
   const unsigned long long per = (total + gridDim.x - 1) / gridDim.x;
   const unsigned long long t0 = (unsigned long long)blockIdx.x * per;
   const unsigned long long t1 = min(t0 + per, total);
-  for (int i = tid; i < kHbWarps * 257; i += blockDim.x) (&sh[0][0])[i] = 0;
-  __syncthreads();
   if (t0 >= t1) return;
-  uint32_t* my = sh[tid >> 5];
+  zero_cols(hc_sm, warp, lane);
+  __syncwarp();
+  const uint32_t col = lane_col(hc_sm, warp, lane);
   int s = 0;
   {
     int lo = 0, hi = n_shards - 1;
@@ -147,48 +138,24 @@ hist_batch_kernel(const qlc_desc* descs, int n_shards, const unsigned long long*
     s = lo;
   }
   int target = shared ? 0 : s;
-  for (unsigned long long t = t0; t < t1; t++) {
+  for (unsigned long long t = t0; t < t1;) {
     while (s + 1 < n_shards && item_base[s + 1] <= t) s++;
     const int tgt = shared ? 0 : s;
-    if (tgt != target) {  // flush into the previous shard's histogram
-      __syncthreads();
-      for (int b = tid; b < 256; b += blockDim.x) {
-        uint32_t v = 0;
-        for (int w = 0; w < kHbWarps; w++) {
-          v += sh[w][b + (b >> 7)];
-          sh[w][b + (b >> 7)] = 0;
-        }
-        if (v) atomicAdd(&hists[(size_t)target * 256 + b], (unsigned long long)v);
-      }
-      __syncthreads();
+    if (tgt != target) {
+      flush_cols(hc_sm, hists + (size_t)target * 256, tid);
       target = tgt;
     }
+    const unsigned long long e = min(t1, item_base[s + 1]);  // this CTA's items of shard s end here
     const qlc_desc d = descs[s];
     const uint8_t* in = static_cast<const uint8_t*>(d.in);
-    const uint64_t beg = (t - item_base[s]) * kHistItem;
-    const uint64_t end = min(beg + kHistItem, d.in_bytes);
-    const uint4* v = reinterpret_cast<const uint4*>(in + beg);
-    const uint64_t nvec = (end - beg) / 16;
-    uint64_t i = tid;
-    for (; i + (kHbUnroll - 1) * blockDim.x < nvec; i += kHbUnroll * blockDim.x) {
-      uint4 q[kHbUnroll];  // kHbUnroll loads in flight per thread
-#pragma unroll
-      for (int u = 0; u < kHbUnroll; u++) q[u] = ldg_nc_v4(v + i + u * blockDim.x);
-#pragma unroll
-      for (int u = 0; u < kHbUnroll; u++) count16_batch(my, q[u]);
-    }
-    for (; i < nvec; i += blockDim.x) count16_batch(my, ldg_nc_v4(v + i));
-    for (uint64_t i = beg + nvec * 16 + tid; i < end; i += blockDim.x) {
-      const uint32_t b = in[i];
-      atomicAdd(&my[b + (b >> 7)], 1u);
-    }
+    const uint64_t beg = (t - item_base[s]) * kHistItem;      // a multiple of 16
+    const uint64_t end = min((uint64_t)((e - item_base[s]) * kHistItem), (uint64_t)d.in_bytes);
+    const uint64_t vb = beg / 16, ve = end / 16;
+    count_span(reinterpret_cast<const uint4*>(in) + vb, ve - vb, col, tid);
+    count_bytes(in + ve * 16, end - ve * 16, col, tid);
+    t = e;
   }
-  __syncthreads();
-  for (int b = tid; b < 256; b += blockDim.x) {
-    uint32_t v = 0;
-    for (int w = 0; w < kHbWarps; w++) v += sh[w][b + (b >> 7)];
-    if (v) atomicAdd(&hists[(size_t)target * 256 + b], (unsigned long long)v);
-  }
+  flush_cols(hc_sm, hists + (size_t)target * 256, tid);
 }
 
 }  // namespace qlc
@@ -210,13 +177,15 @@ qlc_status qlc_histogram_batch(const qlc_desc* d_descs, int n_shards, uint64_t* 
   if (!aligned(d_ws, 16) || !aligned(d_descs, 16) || !aligned(d_hists, 8)) return QLC_ERR_ARG;
   BatchWs w;
   if (!batch_ws_layout(d_ws, ws_bytes, n_shards, &w)) return QLC_ERR_CAPACITY;
+  static int smem_done[64] = {0};
+  if (!hist_cols_smem_ok(hist_batch_kernel, smem_done)) return QLC_ERR_CUDA;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t hist_bytes = (size_t)(shared ? 1 : n_shards) * 256 * sizeof(uint64_t);
   if (cudaMemsetAsync(d_hists, 0, hist_bytes, st) != cudaSuccess) return QLC_ERR_CUDA;
   // histogram errors (misaligned shards) have no status word: they are
   // reported as QLC_ERR_ARG by the encode plan of the same descriptors
   plan_kernel<<<1, kPlanThreads, 0, st>>>(kPlanHistogram, d_descs, n_shards, 0, w, nullptr);
-  hist_batch_kernel<<<sm_count() * 4, kHbWarps * 32, 0, st>>>(
+  hist_batch_kernel<<<sm_count() * kHcBatchWaves, kHcThreads, kHcSmemBytes, st>>>(
       d_descs, n_shards, w.item_base, reinterpret_cast<unsigned long long*>(d_hists), shared ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }

@@ -1,62 +1,29 @@
 // hist_lut.cu -- byte histogram (Section 4) and LUT construction (Section 7)
 // kernels of libqlc, plus their C-ABI entry points.
-#include "qlc_common.cuh"
+#include "hist_cols.cuh"
 
 #include <algorithm>
 #include <functional>
 
 namespace qlc {
 
-constexpr int kHistWarps = 8;
-constexpr int kHistThreads = kHistWarps * 32;
-constexpr int kHistUnroll = 4;
-
-// Per-warp shared histograms, indexed with the bin's bit 7 folded into the
-// bank (b + (b >> 7)) so that a value and its negation (b, b ^ 0x80), which
-// are about equally frequent in sign-symmetric data, sit in different banks.
-__device__ __forceinline__ void count16(uint32_t* h, uint4 q) {
-  uint32_t w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-  for (int k = 0; k < 4; k++) {
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      uint32_t b = (w[k] >> (8 * j)) & 0xFFu;
-      atomicAdd(&h[b + (b >> 7)], 1u);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kHistThreads)
+// One CTA of seven warps per SM counts a contiguous slice of the tensor into
+// lane-private columns (hist_cols.cuh); the last CTA also counts the bytes
+// after the last whole 16-byte vector.
+__global__ void __launch_bounds__(kHcThreads, 1)
 hist_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __restrict__ hist) {
-  __shared__ uint32_t sh[kHistWarps][257];
-  for (int i = threadIdx.x; i < kHistWarps * 257; i += kHistThreads) (&sh[0][0])[i] = 0;
-  __syncthreads();
-  uint32_t* my = sh[threadIdx.x >> 5];
-  const uint4* v = reinterpret_cast<const uint4*>(in);
+  extern __shared__ __align__(16) uint32_t hc_sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  zero_cols(hc_sm, warp, lane);
+  __syncwarp();
+  const uint32_t col = lane_col(hc_sm, warp, lane);
   const uint64_t nvec = n / 16;
-  const uint64_t stride = (uint64_t)gridDim.x * kHistThreads;
-  uint64_t i = (uint64_t)blockIdx.x * kHistThreads + threadIdx.x;
-  for (; i + (kHistUnroll - 1) * stride < nvec; i += kHistUnroll * stride) {
-    uint4 q[kHistUnroll];
-#pragma unroll
-    for (int u = 0; u < kHistUnroll; u++) q[u] = ldg_nc_v4(v + i + u * stride);
-#pragma unroll
-    for (int u = 0; u < kHistUnroll; u++) count16(my, q[u]);
-  }
-  for (; i < nvec; i += stride) count16(my, ldg_nc_v4(v + i));
-  if (blockIdx.x == 0) {
-    for (uint64_t t = nvec * 16 + threadIdx.x; t < n; t += kHistThreads) {
-      uint32_t b = in[t];
-      atomicAdd(&my[b + (b >> 7)], 1u);
-    }
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < 256; b += kHistThreads) {
-    uint32_t s = 0;
-#pragma unroll
-    for (int w = 0; w < kHistWarps; w++) s += sh[w][b + (b >> 7)];
-    if (s) atomicAdd(&hist[b], (unsigned long long)s);
-  }
+  const uint64_t per = (nvec + gridDim.x - 1) / gridDim.x;
+  const uint64_t beg = (uint64_t)blockIdx.x * per;
+  const uint64_t end = min(beg + per, nvec);
+  if (beg < end) count_span(reinterpret_cast<const uint4*>(in) + beg, end - beg, col, tid);
+  if (blockIdx.x == gridDim.x - 1) count_bytes(in + nvec * 16, n - nvec * 16, col, tid);
+  flush_cols(hc_sm, hist, tid);
 }
 
 // Rank of symbol s (Section 7): symbols with a larger count, or the same
@@ -209,15 +176,21 @@ qlc_status qlc_histogram(const uint8_t* d_in, size_t n, uint64_t* d_hist, int ac
                          qlc_stream_t stream) {
   if (!d_hist || (n > 0 && !d_in)) return QLC_ERR_ARG;
   if (!aligned(d_in, 16) || !aligned(d_hist, 8)) return QLC_ERR_ARG;
+  static int smem_done[64] = {0};
+  if (!hist_cols_smem_ok(hist_kernel, smem_done)) return QLC_ERR_CUDA;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (!accumulate && cudaMemsetAsync(d_hist, 0, 256 * sizeof(uint64_t), st) != cudaSuccess)
     return QLC_ERR_CUDA;
   if (n == 0) return QLC_OK;
+  // one CTA per SM, at least 48 KiB each; a CTA counts under 2^31 bytes
   const uint64_t nvec = n / 16;
-  uint64_t want = (nvec + kHistThreads - 1) / kHistThreads;
-  uint64_t cap = (uint64_t)sm_count() * 6;
-  int grid = (int)(want < 1 ? 1 : (want < cap ? want : cap));
-  hist_kernel<<<grid, kHistThreads, 0, st>>>(d_in, n, reinterpret_cast<unsigned long long*>(d_hist));
+  uint64_t grid = (nvec + 3071) / 3072;
+  const uint64_t cap = (uint64_t)sm_count();
+  if (grid > cap) grid = cap;
+  const uint64_t floor_grid = (nvec >> 27) + 1;
+  if (grid < floor_grid) grid = floor_grid;
+  if (grid > 0x7fffffffu) return QLC_ERR_ARG;
+  hist_kernel<<<(int)grid, kHcThreads, kHcSmemBytes, st>>>(d_in, n, reinterpret_cast<unsigned long long*>(d_hist));
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
 

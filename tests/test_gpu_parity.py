@@ -132,6 +132,18 @@ def test_histogram_accumulate(qlc):
     assert np.array_equal(h.cpu().numpy().astype(np.uint64), want)
 
 
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 3072 * 16 - 1, 3072 * 16, 3072 * 16 + 1, 2 * 3072 * 16 + 9,
+                               152 * 3072 * 16 - 16, 152 * 3072 * 16 + 17, 10_000_019, 64 * 2**20 + 3])
+def test_histogram_grid_sizes(qlc, n):
+    """The histogram's grid is one CTA per 48 KiB of input up to one per SM;
+    sizes around those steps, with ragged slices and tails, count exactly."""
+    for kind in ("t4", "constant", "uniform_bytes"):
+        x = inputs.make_e4m3(kind, n, seed=n % 1000)
+        h = torch.full((256,), 7, dtype=torch.int64, device="cuda")
+        qlc.qlc_histogram(x.cuda(), h)
+        assert np.array_equal(h.cpu().numpy().astype(np.uint64), oracle.histogram(x.numpy())), kind
+
+
 def test_build_lut_best_picks_fewer_bits(qlc):
     for kind in ("t4", "relu_t4"):
         x = inputs.make_e4m3(kind, 200_000, seed=3).numpy()
