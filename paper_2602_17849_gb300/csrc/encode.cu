@@ -256,7 +256,10 @@ struct Packer {
 #pragma unroll
     for (int k = 0; k < 8; k++) {
       const uint32_t e0 = e[2 * k], e1 = e[2 * k + 1];
-      P[k] = (e0 & ~31u) | __funnelshift_r(e1 & ~31u, 0u, e0);  // second code right after the first
+      // second code right after the first: e1 >> len0 also moves e1's length
+      // field down to bits 0..3-len0, which the mask clears with e0's (the pair
+      // itself, at most 22 bits, sits at bits 31..10)
+      P[k] = (e0 | __funnelshift_r(e1, 0u, e0)) & ~31u;
       L8[k] = (e0 + e1) & 31u;  // the two lengths; code bits sit above bit 20
       L += L8[k];
     }
