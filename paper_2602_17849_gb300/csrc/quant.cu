@@ -37,6 +37,27 @@ __device__ __forceinline__ uint32_t e4m3_rne(float v) {
   return min(code, 0x7Fu) | ((u >> 24) & 0x80u);
 }
 
+// The same rounding of q0 = x * (1 / scale), which is not the quotient the
+// rule names (x / scale, rounded once) but lies within 2^-23 |x / scale| of
+// it: both 1 / scale and the product are rounded to nearest.  The code is a
+// step function of the value whose steps sit at the midpoints between
+// neighbouring e4m3 magnitudes, exact fp32 numbers, so q0 and the rounded
+// quotient get the same code unless one of them lies within 2^-22 |q0| of a
+// midpoint.  In grid units (t = |q0| 2^(3-k), |q0| < 2^(k+1)) that margin is
+// under 2^-18 of a step; *near is set when t lies within 2^-17 of a midpoint,
+// and the caller then takes the exact division.  Outside the margin the code
+// is the rule's, so the result is exact either way.
+__device__ __forceinline__ uint32_t e4m3_rne_or_near(float q0, bool* near) {
+  const uint32_t u = __float_as_uint(q0);
+  const int e = (int)((u >> 23) & 0xFFu) - 127;
+  const int k = max(e, -6);
+  const float t = fabsf(q0) * __uint_as_float((uint32_t)(130 - k) << 23);
+  const float rt = rintf(t);
+  *near = fabsf(t - rt) > 0.5f - 0x1p-17f;  // t - rt is exact
+  const uint32_t code = (uint32_t)(8 * k + 48) + (uint32_t)rt;
+  return min(code, 0x7Fu) | ((u >> 24) & 0x80u);
+}
+
 template <int kDtype>
 struct QuantIo;
 
@@ -117,9 +138,25 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
 #pragma unroll
       for (int o = 1; o < kLanesPerBlock; o <<= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
       const float scale = amax / 480.0f;
+      // one reciprocal per lane and block; a scale below 2^-125 (whose
+      // reciprocal could overflow) takes the exact division for every element
+      const float y = 1.0f / scale;
+      const bool by_product = scale >= 0x1p-125f;
       uint32_t c[E];
+      bool exact = !by_product;
 #pragma unroll
-      for (int j = 0; j < E; j++) c[j] = scale > 0.0f ? e4m3_rne(v[u][j] / scale) : 0u;
+      for (int j = 0; j < E; j++) {
+        bool near;
+        c[j] = e4m3_rne_or_near(v[u][j] * y, &near);
+        exact |= near;
+      }
+      if (!(scale > 0.0f)) {
+#pragma unroll
+        for (int j = 0; j < E; j++) c[j] = 0u;
+      } else if (exact) {  // rare: one branch per lane and block
+#pragma unroll
+        for (int j = 0; j < E; j++) c[j] = e4m3_rne(v[u][j] / scale);
+      }
       if (i < n && (lane % kLanesPerBlock) == 0) scales[i / 32] = scale;
       if (i + E <= n) {
         if (E == 4) {

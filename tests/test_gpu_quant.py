@@ -186,3 +186,38 @@ def test_full_size_fused_sampled(qlc):
     want = oracle.dequantize_block32(oc, osc)
     got = y.view(-1, 32)[torch.from_numpy(blocks).cuda()].cpu().numpy().reshape(-1)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def _near_midpoint_blocks(n_blocks, seed, lo=-80.0, hi=80.0):
+    """Blocks whose quotients x / scale sit on, or within 4 ulps of, the
+    midpoints between neighbouring e4m3 magnitudes (where rounding x / scale
+    and rounding a nearby value can differ).  Element 0 of a block is its
+    absmax, which fixes the block's scale; scales are log-uniform over
+    [2^lo, 2^hi]."""
+    rng = np.random.default_rng(seed)
+    mags = np.array([oracle.e4m3_value(c) for c in range(0x80)], np.float64)
+    mids = (mags[:-1] + mags[1:]) / 2
+    x = np.zeros((n_blocks, 32), np.float32)
+    for b in range(n_blocks):
+        amax = np.float32(480.0 * 2.0 ** rng.uniform(lo, hi))
+        scale = np.float32(amax / np.float32(480.0))
+        m = mids[rng.integers(len(mids), size=31)]
+        v = (m * np.float64(scale)).astype(np.float32)
+        v = (v.view(np.int32) + rng.integers(-4, 5, size=31).astype(np.int32)).view(np.float32)
+        v = np.minimum(np.abs(v), amax) * np.where(rng.random(31) < 0.5, -1, 1).astype(np.float32)
+        x[b, 0] = amax * (1 if rng.random() < 0.5 else -1)
+        x[b, 1:] = v
+    return x.reshape(-1)
+
+
+@pytest.mark.parametrize("lo,hi", [(-80.0, 80.0), (-125.5, -124.5), (-130.0, -120.0)])
+def test_quantize_near_midpoints(qlc, lo, hi):
+    """Quotients on and next to the rounding midpoints (and scales around the
+    2^-125 limit of the reciprocal) quantise exactly as the oracle does."""
+    x = _near_midpoint_blocks(4096, seed=int(lo * 10) & 0xFFFF, lo=lo, hi=hi)
+    st, codes, scales, hist = _gpu_quantize(qlc, torch.from_numpy(x))
+    ost, ocodes, oscales = oracle.quantize_block32(x)
+    assert st == ost == 0
+    assert np.array_equal(scales.view(np.uint32), oscales.view(np.uint32))
+    assert np.array_equal(codes, ocodes)
+    assert np.array_equal(hist, oracle.histogram(ocodes))
