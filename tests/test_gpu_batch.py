@@ -182,3 +182,46 @@ def test_full_size_batched_large_shared_and_per_shard(qlc):
     arena, shards = inputs.cfg4_batch("cuda")
     _full_batch_check(qlc, shards, 4096, True, [0, 63])
     _full_batch_check(qlc, shards, 4096, False, [31])
+
+
+def test_full_size_batched_large_compressibility_vs_huffman(qlc):
+    """64 x 64 MiB Laplace with 1% outliers, coded with one shared LUT and with
+    a LUT per shard.  Against the oracle's Huffman code and Shannon entropy of
+    the same PMFs (Section 4): entropy bound >= Huffman >= QLC code >= QLC
+    container, the container's index and padding cost at most 0.1 pp, and the
+    per-shard LUTs compress at least as well as the shared one.  The device
+    histograms equal the oracle's."""
+    arena, shards = inputs.cfg4_batch("cuda")
+    sizes = [x.numel() for x in shards]
+    n = sum(sizes)
+    hs = [oracle.histogram(_host(x)) for x in shards]
+    h_all = np.sum(hs, axis=0).astype(np.uint64)
+    got = {}
+    for shared in (True, False):
+        b = qlc.Batch(shards, 4096, schemes=(1,), shared_lut=shared)
+        b.encode()
+        torch.cuda.synchronize()
+        b.check()
+        gh = _host(b.hists).view(np.int64).reshape(-1, 256).astype(np.uint64)
+        lens = (_host(b.luts).reshape(-1, qlc.LUT_BYTES)[:, 32:544].copy().view(np.uint16) & 15).astype(np.uint64)
+        if shared:
+            assert np.array_equal(gh[0], h_all)
+            code_bits = int((h_all * lens[0]).sum())
+        else:
+            assert all(np.array_equal(gh[i], hs[i]) for i in range(len(shards)))
+            code_bits = int(sum((hs[i] * lens[i]).sum() for i in range(len(shards))))
+        c = int(_host(b.c_bytes).sum())
+        got[shared] = (1 - c / n, 1 - code_bits / (8 * n))
+        del b
+    ent = {True: 1 - oracle.entropy(h_all) / 8,
+           False: 1 - sum(oracle.entropy(h) * s for h, s in zip(hs, sizes)) / (8 * n)}
+    huf = {True: 1 - oracle.huffman_bits(h_all) / (8 * n),
+           False: 1 - sum(oracle.huffman_bits(h) for h in hs) / (8 * n)}
+    for shared in (True, False):
+        container, code = got[shared]
+        print(f"\n64 x 64 MiB Laplace + 1% outliers, {'shared LUT' if shared else 'per-shard LUTs'}: "
+              f"entropy bound {100 * ent[shared]:.3f} %, Huffman {100 * huf[shared]:.3f} %, "
+              f"QLC code {100 * code:.3f} %, QLC container {100 * container:.3f} %")
+        assert ent[shared] >= huf[shared] >= code >= container > 0
+        assert code - container <= 0.001
+    assert got[False][1] >= got[True][1]
