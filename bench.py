@@ -275,6 +275,48 @@ def e2e_leg(dev, x, steps: int, slots: int = 3):
             "serial_gbs": n / statistics.median(lat) / 1e9}
 
 
+def large_leg(dev, steps: int, warmup: int, peak: float):
+    """Batched large: 64 shards x 64 MiB of Laplace(b=1) with 1 % N(0, 20^2)
+    outliers, encoded and decoded as one batch (one CUDA graph per direction),
+    with one shared LUT and with one LUT per shard."""
+    import torch
+
+    from paper_2602_17849_gb300 import inputs, qlc
+    arena, shards = inputs.cfg4_batch(dev)
+    total = sum(x.numel() for x in shards)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    out = {"workload": "64 shards x 64 MiB, Laplace(b=1) + 1 % N(0, 20^2) outliers, e4m3, chunk 4096"}
+    for shared in (True, False):
+        b = qlc.Batch(shards, 4096, schemes=(1,), shared_lut=shared)
+        b.capture()
+        enc_ms = timed(lambda: b.replay("encode"))
+        dec_ms = timed(lambda: b.replay("decode"))
+        b.check()
+        exact = all(torch.equal(b.output(i), x) for i, x in enumerate(shards))
+        c = int(b.c_bytes.sum().item())
+        out["shared_lut" if shared else "per_shard_lut"] = {
+            "encode_ms": enc_ms, "decode_ms": dec_ms,
+            "encode_gbs": total / (enc_ms * 1e-3) / 1e9, "decode_gbs": total / (dec_ms * 1e-3) / 1e9,
+            "encode_roofline_frac": (2 * total + c) / (enc_ms * 1e-3) / 1e9 / peak,
+            "decode_roofline_frac": (total + c) / (dec_ms * 1e-3) / 1e9 / peak,
+            "compressibility": 1 - c / total, "bit_exact": exact}
+        del b
+    return out
+
+
 def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152):
     """The batched workload (1152 shards, 64 KiB - 16 MiB, t4 / gauss / laplace,
     per-shard LUTs): one CUDA graph per direction with the autotuned launch
@@ -479,6 +521,7 @@ def main():
                     help="seconds of oracle work for cpu_baseline (0 = skip)")
     ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-batched", action="store_true", help="skip the 1152-shard batched leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 64 x 64 MiB batched leg")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving leg length (0 = skip)")
     ap.add_argument("--no-fused", action="store_true", help="skip the fused quantise / dequantise leg")
     ap.add_argument("--fused-elems", type=int, default=N_BYTES,
@@ -605,6 +648,8 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.batched_shards)
+    if not args.no_large:
+        line["batched_large"] = large_leg(dev, max(3, args.steps // 2), args.warmup, peak)
     if not args.no_fused:
         line["fused_quantize"] = fused_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.fused_elems)
     if args.serve_seconds > 0:
