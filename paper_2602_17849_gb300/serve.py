@@ -190,28 +190,47 @@ class Server:
 
 
 def run_poisson(server: Server, make_request, rate_hz: float, duration_s: float, seed: int,
-                sleep: Callable[[float], None] = lambda s: None):
+                sleep: Callable[[float], None] = lambda s: None, young_gc_every: int = 0):
     """Drive the server with Poisson arrivals for duration_s seconds of server
     clock; make_request(i, arrival, rng) builds request i.  Returns the list
-    of requests in arrival order."""
+    of requests in arrival order.
+
+    young_gc_every > 0: Python's automatic collection is off for the run and
+    only the young generation is collected, every young_gc_every loop
+    iterations.  A full collection walks every live request and stalled the
+    loop for tens of milliseconds, which set the p99 latency; a young one
+    takes well under a millisecond.  The collector is switched back on
+    afterwards if it was on."""
+    import gc
+
     import numpy as np
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate_hz, size=int(rate_hz * duration_s * 1.5) + 16)
     arrivals = np.cumsum(gaps)
     arrivals = arrivals[arrivals < duration_s]
     reqs = []
-    t0 = server.clock()
-    i = 0
-    while i < len(arrivals) or not server.idle():
-        now = server.clock() - t0
-        while i < len(arrivals) and arrivals[i] <= now:
-            r = make_request(i, t0 + float(arrivals[i]), rng)
-            reqs.append(r)
-            server.submit(r)
-            i += 1
-        server.step()
-        if i < len(arrivals) and server.idle():
-            sleep(max(0.0, float(arrivals[i]) - (server.clock() - t0)))
+    gc_on = gc.isenabled()
+    if young_gc_every > 0:
+        gc.disable()
+    try:
+        t0 = server.clock()
+        i = k = 0
+        while i < len(arrivals) or not server.idle():
+            now = server.clock() - t0
+            while i < len(arrivals) and arrivals[i] <= now:
+                r = make_request(i, t0 + float(arrivals[i]), rng)
+                reqs.append(r)
+                server.submit(r)
+                i += 1
+            server.step()
+            k += 1
+            if young_gc_every > 0 and k % young_gc_every == 0:
+                gc.collect(0)
+            if i < len(arrivals) and server.idle():
+                sleep(max(0.0, float(arrivals[i]) - (server.clock() - t0)))
+    finally:
+        if young_gc_every > 0 and gc_on:
+            gc.enable()
     return reqs
 
 
@@ -231,11 +250,16 @@ class CudaExecutor:
     device_arena: CUDA uint8 tensor of the budget's size; the Server's Arena
     hands out byte offsets into it.  A request's block is charged for its
     input, its output and its share of workspace (the admission budget covers
-    in + out + workspace); the output (and its size word) sit at the block's
-    start.  Small per-batch scratch (descriptors, histograms, LUTs, workspace)
-    is allocated with the batch and freed when it completes."""
+    in + out + workspace); the output sits at the block's start.  Small
+    per-batch scratch (descriptors, histograms, LUTs, workspace, the status
+    word and the output sizes) is allocated with the batch and freed when it
+    completes.  Each stream owns two pinned host buffers: descriptors go up
+    from one without a host wait, and the batch's status word and output
+    sizes come back into the other, copied before the batch's completion
+    event, so finishing a batch reads host memory only."""
 
-    def __init__(self, pool, device_arena, chunk_symbols: int = 4096, schemes=(1,), n_streams: int = 4):
+    def __init__(self, pool, device_arena, chunk_symbols: int = 4096, schemes=(1,), n_streams: int = 4,
+                 max_batch: int = 4096):
         import torch
 
         from . import qlc
@@ -244,9 +268,13 @@ class CudaExecutor:
         self.dev_arena = device_arena
         self.cs = chunk_symbols
         self.schemes = list(schemes)
+        self.max_batch = max_batch
         self.streams = [torch.cuda.Stream(device=pool.device) for _ in range(n_streams)]
         self.free_streams = list(range(n_streams))
         self.base = device_arena.data_ptr()
+        # per stream: descriptor rows (qlc_desc = 6 x 64-bit) and [status, sizes...] per part
+        self.pin_desc = [torch.empty(max_batch * 6, dtype=torch.int64, pin_memory=True) for _ in range(n_streams)]
+        self.pin_meta = [torch.empty(max_batch + 2, dtype=torch.int64, pin_memory=True) for _ in range(n_streams)]
 
     def out_bytes(self, req: Request) -> int:
         if req.kind == "compress":
@@ -258,46 +286,57 @@ class CudaExecutor:
         n_sym = req.n_in if req.kind == "compress" else req.n_out
         ws = q.qlc_batch_workspace_size(1, n_sym, self.cs if req.kind == "compress" else 128)
         extra = (256 * 8 + q.LUT_BYTES) if req.kind == "compress" else 0
-        return _al(self.out_bytes(req)) + _al(8) + _al(req.n_in) + _al(ws + extra)
+        return _al(self.out_bytes(req)) + _al(req.n_in) + _al(ws + extra)
 
     def launch(self, batch):
         torch, q = self.torch, self.qlc
+        if len(batch) > self.max_batch:
+            raise ValueError("batch larger than the executor's max_batch")
         dev = self.pool.device
         sid = self.free_streams.pop(0)
         st = self.streams[sid]
         handle = {"stream": sid, "event": torch.cuda.Event(), "parts": []}
         pool_base = self.pool.data_ptr()
+        rows_np = self.pin_desc[sid].numpy().reshape(-1, 6)
+        pin_meta = self.pin_meta[sid]
+        row0 = meta0 = 0
         with torch.cuda.stream(st):
             for kind in ("compress", "decompress"):
                 reqs = [r for r in batch if r.kind == kind]
                 if not reqs:
                     continue
                 n = len(reqs)
-                status = torch.zeros(1, dtype=torch.int32, device=dev)
-                rows = []
+                meta = torch.zeros(n + 1, dtype=torch.int64, device=dev)  # status word, then sizes
+                status = meta[:1].view(torch.int32)[:1]
+                mp = meta.data_ptr()
                 if kind == "compress":
                     luts = torch.empty(n * q.LUT_BYTES, dtype=torch.uint8, device=dev)
                     hists = torch.empty(n * 256, dtype=torch.int64, device=dev)
-                    for i, r in enumerate(reqs):
-                        cap = self.out_bytes(r)
-                        rows.append((pool_base + r.in_ref, r.n_in, self.base + r.out_off, cap,
-                                     luts.data_ptr() + i * q.LUT_BYTES, self.base + r.out_off + _al(cap)))
-                    total = sum(r.n_in for r in reqs)
-                    ws = torch.empty(q.qlc_batch_workspace_size(n, total, self.cs), dtype=torch.uint8, device=dev)
-                    descs = q.descs_tensor(rows, dev)
+                    lp = luts.data_ptr()
+                    rows = [(pool_base + r.in_ref, r.n_in, self.base + r.out_off, self.out_bytes(r),
+                             lp + i * q.LUT_BYTES, mp + 8 * (i + 1)) for i, r in enumerate(reqs)]
+                    ws = torch.empty(q.qlc_batch_workspace_size(n, sum(r.n_in for r in reqs), self.cs),
+                                     dtype=torch.uint8, device=dev)
+                else:
+                    rows = [(pool_base + r.in_ref, r.n_in, self.base + r.out_off, r.n_out, 0, mp + 8 * (i + 1))
+                            for i, r in enumerate(reqs)]
+                    ws = torch.empty(q.qlc_batch_workspace_size(n, sum(r.n_out for r in reqs), 128),
+                                     dtype=torch.uint8, device=dev)
+                rows_np[row0:row0 + n] = rows
+                descs = torch.empty(n * 48, dtype=torch.uint8, device=dev)
+                descs.copy_(self.pin_desc[sid][row0 * 6:(row0 + n) * 6].view(torch.uint8), non_blocking=True)
+                if kind == "compress":
                     q.qlc_histogram_batch(descs, n, hists, False, ws, stream=st)
                     q.qlc_build_lut_batch(hists, n, self.schemes, luts, stream=st)
                     q.qlc_encode_batch(descs, n, self.cs, ws, status, stream=st)
-                    handle["parts"].append((kind, reqs, status, (descs, luts, hists, ws)))
+                    keep = (descs, meta, luts, hists, ws)
                 else:
-                    for r in reqs:
-                        rows.append((pool_base + r.in_ref, r.n_in, self.base + r.out_off, r.n_out, 0,
-                                     self.base + r.out_off + _al(r.n_out)))
-                    total = sum(r.n_out for r in reqs)
-                    ws = torch.empty(q.qlc_batch_workspace_size(n, total, 128), dtype=torch.uint8, device=dev)
-                    descs = q.descs_tensor(rows, dev)
                     q.qlc_decode_batch(descs, n, ws, status, stream=st)
-                    handle["parts"].append((kind, reqs, status, (descs, ws)))
+                    keep = (descs, meta, ws)
+                pin_meta[meta0:meta0 + n + 1].copy_(meta, non_blocking=True)
+                handle["parts"].append((kind, reqs, meta0, keep))
+                row0 += n
+                meta0 += n + 1
             handle["event"].record(st)
         return handle
 
@@ -305,15 +344,12 @@ class CudaExecutor:
         return handle["event"].query()
 
     def finish(self, handle, batch) -> None:
-        torch = self.torch
-        for kind, reqs, status, _keep in handle["parts"]:
-            st = int(status.item())
-            for r in reqs:
+        meta = self.pin_meta[handle["stream"]].numpy()
+        for kind, reqs, m0, _keep in handle["parts"]:
+            st = int(meta[m0]) & 0xFFFFFFFF
+            for i, r in enumerate(reqs):
                 r.status = st
-                cap = self.out_bytes(r)
-                size_at = r.out_off + _al(cap)
-                nb = int(self.dev_arena[size_at:size_at + 8].view(torch.int64).item())
-                r.result = (r.out_off, nb)   # output bytes at this arena offset
+                r.result = (r.out_off, int(meta[m0 + 1 + i]))   # output bytes at this arena offset
         self.free_streams.append(handle["stream"])
 
     def result_bytes(self, req: Request):
@@ -383,11 +419,11 @@ def serve_run(device, rate_hz: float, duration_s: float, budget_bytes: int, work
     import torch
     arena_t = torch.empty(budget_bytes, dtype=torch.uint8, device=device)
     ex = CudaExecutor(workload.pool, arena_t, chunk_symbols=chunk_symbols, n_streams=n_streams)
-    srv = Server(ex, budget_bytes, max_in_flight=n_streams,
+    srv = Server(ex, budget_bytes, max_in_flight=n_streams, max_batch=ex.max_batch,
                  on_complete=(lambda r: on_complete(r, ex)) if on_complete else None)
     t0 = time.perf_counter()
     reqs = run_poisson(srv, workload.make_request, rate_hz, duration_s, seed,
-                       sleep=lambda s: time.sleep(min(s, 0.0005)))
+                       sleep=lambda s: time.sleep(min(s, 0.0005)), young_gc_every=64)
     srv.drain()
     torch.cuda.synchronize()
     return reqs, ex, srv, time.perf_counter() - t0

@@ -112,29 +112,32 @@ def test_reject_too_large_and_cancel_frees():
     assert {r.rid for r in srv.completed} == {1, 3}
 
 
+def _run_mix(young_gc_every=0):
+    """A 50 ms Poisson run at 20k requests/s on the fake executor."""
+    clock = FakeClock()
+    ex = FakeExecutor(clock, delay=0.001)
+    srv = Server(ex, budget_bytes=4 << 20, max_in_flight=4, clock=clock)
+
+    def make(i, arrival, rng):
+        n = int(np.exp(rng.uniform(np.log(4096), np.log(1 << 20))))
+        kind = "compress" if rng.random() < 0.5 else "decompress"
+        return Request(i, kind, n, n // 2, int(rng.integers(0, 1 << 30)), arrival)
+
+    def tick(_):
+        clock.t += 0.0002
+    orig = srv.step
+
+    def step():
+        orig()
+        clock.t += 0.0001
+    srv.step = step
+    reqs = run_poisson(srv, make, rate_hz=20_000, duration_s=0.05, seed=3000, sleep=tick,
+                       young_gc_every=young_gc_every)
+    return reqs, ex
+
+
 def test_continuous_batching_results_independent_of_mix():
-    def run(subset=None):
-        clock = FakeClock()
-        ex = FakeExecutor(clock, delay=0.001)
-        srv = Server(ex, budget_bytes=4 << 20, max_in_flight=4, clock=clock)
-
-        def make(i, arrival, rng):
-            n = int(np.exp(rng.uniform(np.log(4096), np.log(1 << 20))))
-            kind = "compress" if rng.random() < 0.5 else "decompress"
-            return Request(i, kind, n, n // 2, int(rng.integers(0, 1 << 30)), arrival)
-
-        def tick(_):
-            clock.t += 0.0002
-        orig = srv.step
-
-        def step():
-            orig()
-            clock.t += 0.0001
-        srv.step = step
-        reqs = run_poisson(srv, make, rate_hz=20_000, duration_s=0.05, seed=3000, sleep=tick)
-        return reqs, ex
-
-    reqs, ex = run()
+    reqs, ex = _run_mix()
     assert len(reqs) > 500 and all(r.done is not None for r in reqs)
     assert len(ex.launches) > 1 and max(len(b) for b in ex.launches) > 1
     lat = percentiles([r.latency for r in reqs])
@@ -164,3 +167,17 @@ def test_drain_times_out_when_a_batch_never_finishes():
     srv.clock = ticking
     with pytest.raises(TimeoutError):
         srv.drain(timeout_s=5.0)
+
+
+def test_run_with_young_gc_only_restores_the_collector_and_changes_no_result():
+    """With automatic collection off and young-generation collections only,
+    the same arrivals give the same batches and results, and the collector is
+    on again afterwards, with nothing frozen or unfrozen."""
+    import gc
+    assert gc.isenabled()
+    frozen = gc.get_freeze_count()
+    a, ex_a = _run_mix(0)
+    b, ex_b = _run_mix(8)
+    assert gc.isenabled() and gc.get_freeze_count() == frozen
+    assert [r.result for r in a] == [r.result for r in b]
+    assert [len(x) for x in ex_a.launches] == [len(x) for x in ex_b.launches]
