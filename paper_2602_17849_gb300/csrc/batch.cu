@@ -173,6 +173,7 @@ size_t qlc_batch_workspace_size(int n_shards, uint64_t total_symbols, uint32_t c
 
 qlc_status qlc_histogram_batch(const qlc_desc* d_descs, int n_shards, uint64_t* d_hists, int shared,
                                void* d_ws, size_t ws_bytes, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_histogram_batch");
   if (!d_descs || n_shards < 1 || !d_hists || !d_ws) return QLC_ERR_ARG;
   if (!aligned(d_ws, 16) || !aligned(d_descs, 16) || !aligned(d_hists, 8)) return QLC_ERR_ARG;
   BatchWs w;

@@ -531,6 +531,7 @@ static int decode_grid(uint64_t out_cap) {
 
 extern "C" qlc_status qlc_decode(const uint8_t* d_in, size_t in_bytes, uint8_t* d_out, size_t out_cap,
                                  uint64_t* d_n_out, uint32_t* d_status, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_decode");
   if (!d_in || !d_n_out || (out_cap > 0 && !d_out)) return QLC_ERR_ARG;
   if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_n_out, 8) || !aligned(d_status, 4))
     return QLC_ERR_ARG;
@@ -542,6 +543,7 @@ extern "C" qlc_status qlc_decode(const uint8_t* d_in, size_t in_bytes, uint8_t* 
 extern "C" qlc_status qlc_decode_dequantize(const uint8_t* d_in, size_t in_bytes, const float* d_scales,
                                             void* d_out, qlc_dtype dtype, size_t out_cap, uint64_t* d_n_out,
                                             uint32_t* d_status, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_decode_dequantize");
   if (dtype != QLC_DTYPE_F32 && dtype != QLC_DTYPE_BF16) return QLC_ERR_ARG;
   if (!d_in || !d_n_out || (out_cap > 0 && (!d_out || !d_scales))) return QLC_ERR_ARG;
   if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_scales, 4) || !aligned(d_n_out, 8) ||
@@ -560,6 +562,7 @@ extern "C" qlc_status qlc_decode_dequantize(const uint8_t* d_in, size_t in_bytes
 
 extern "C" qlc_status qlc_decode_batch(const qlc_desc* d_descs, int n_shards, void* d_ws, size_t ws_bytes,
                                        uint32_t* d_status, const qlc_launch* h_launch, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_decode_batch");
   if (!d_descs || n_shards < 1 || !d_ws) return QLC_ERR_ARG;
   if (!aligned(d_ws, 16) || !aligned(d_descs, 16) || !aligned(d_status, 4)) return QLC_ERR_ARG;
   BatchWs w;

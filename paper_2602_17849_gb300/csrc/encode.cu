@@ -599,6 +599,7 @@ static int enc_grid(uint64_t items, const qlc_launch* launch) {
 qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint32_t chunk_symbols,
                       uint8_t* d_out, size_t out_cap, void* d_ws, size_t ws_bytes,
                       uint64_t* d_out_bytes, uint32_t* d_status, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_encode");
   if (!d_lut || !d_out || !d_out_bytes || (n > 0 && (!d_in || !d_ws))) return QLC_ERR_ARG;
   if (!chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
   if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_lut, 16) || !aligned(d_ws, 16) ||
@@ -635,6 +636,7 @@ qlc_status qlc_test_encode_stalled_lookback(const uint8_t* d_in, size_t n, const
                                             uint32_t chunk_symbols, uint8_t* d_out, size_t out_cap,
                                             void* d_ws, size_t ws_bytes, uint64_t* d_out_bytes,
                                             uint32_t* d_status, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_test_encode_stalled_lookback");
   if (!d_in || !d_lut || !d_out || !d_ws || !chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
   if (!aligned(d_in, 16) || !aligned(d_out, 16) || !aligned(d_lut, 16) || !aligned(d_ws, 16) ||
       !aligned(d_out_bytes, 8) || !aligned(d_status, 4))
@@ -665,6 +667,7 @@ qlc_status qlc_test_encode_stalled_lookback(const uint8_t* d_in, size_t n, const
 qlc_status qlc_encode_batch(const qlc_desc* d_descs, int n_shards, uint32_t chunk_symbols, void* d_ws,
                             size_t ws_bytes, uint32_t* d_status, const qlc_launch* h_launch,
                             qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_encode_batch");
   if (!d_descs || n_shards < 1 || !d_ws || !chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
   if (!aligned(d_ws, 16) || !aligned(d_descs, 16) || !aligned(d_status, 4)) return QLC_ERR_ARG;
   BatchWs w;
@@ -727,6 +730,7 @@ extern "C" qlc_status qlc_encode_noalloc(const uint8_t* d_in, size_t n, const ql
                                           uint32_t chunk_symbols, uint8_t* d_out, size_t out_cap,
                                           uint64_t* d_out_bytes, uint32_t* d_status,
                                           qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_encode_noalloc");
   if (!chunk_symbols_ok(chunk_symbols)) return QLC_ERR_ARG;
   const uint64_t n_chunks = (n + chunk_symbols - 1) / chunk_symbols;
   if (n_groups_of(n_chunks) > kNoAllocMaxGroups) return QLC_ERR_CAPACITY;

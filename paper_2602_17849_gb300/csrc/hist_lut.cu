@@ -174,6 +174,7 @@ int qlc_scheme_check(const qlc_scheme* s) { return scheme_valid(s) ? 1 : 0; }
 
 qlc_status qlc_histogram(const uint8_t* d_in, size_t n, uint64_t* d_hist, int accumulate,
                          qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_histogram");
   if (!d_hist || (n > 0 && !d_in)) return QLC_ERR_ARG;
   if (!aligned(d_in, 16) || !aligned(d_hist, 8)) return QLC_ERR_ARG;
   static int smem_done[64] = {0};
@@ -196,6 +197,7 @@ qlc_status qlc_histogram(const uint8_t* d_in, size_t n, uint64_t* d_hist, int ac
 
 qlc_status qlc_build_lut(const uint64_t* d_hist, const qlc_scheme* h_scheme, qlc_lut* d_lut,
                          qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_build_lut");
   if (!d_hist || !d_lut || !scheme_valid(h_scheme)) return QLC_ERR_ARG;
   if (!aligned(d_hist, 8) || !aligned(d_lut, 16)) return QLC_ERR_ARG;
   lut_kernel<<<1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
@@ -205,6 +207,7 @@ qlc_status qlc_build_lut(const uint64_t* d_hist, const qlc_scheme* h_scheme, qlc
 
 qlc_status qlc_build_lut_best(const uint64_t* d_hist, const qlc_scheme* h_schemes, int n_schemes,
                               qlc_lut* d_lut, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_build_lut_best");
   if (!d_hist || !d_lut || !h_schemes || n_schemes < 1 || n_schemes > 8) return QLC_ERR_ARG;
   if (!aligned(d_hist, 8) || !aligned(d_lut, 16)) return QLC_ERR_ARG;
   SchemeSet set;
@@ -220,6 +223,7 @@ qlc_status qlc_build_lut_best(const uint64_t* d_hist, const qlc_scheme* h_scheme
 
 qlc_status qlc_build_lut_batch(const uint64_t* d_hists, int n_luts, const qlc_scheme* h_schemes,
                                int n_schemes, qlc_lut* d_luts, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_build_lut_batch");
   if (!d_hists || !d_luts || !h_schemes || n_luts < 1 || n_schemes < 1 || n_schemes > 8)
     return QLC_ERR_ARG;
   if (!aligned(d_hists, 8) || !aligned(d_luts, 16)) return QLC_ERR_ARG;

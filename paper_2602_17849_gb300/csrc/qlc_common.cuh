@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/qlc.h"
@@ -89,6 +90,16 @@ __device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
 
 // Number of SMs of the current device (cached per device).
 int sm_count();
+
+// A named NVTX range around a host entry point: profilers (nsys, ncu with
+// --nvtx) show the kernels a call launches under the call's name.  Without a
+// profiler attached a push or pop is a call through an empty slot.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ----------------------------------------------------------------- batches
 // Batch workspace: 64 bytes of counters, item_base[n_shards + 1] (first work

@@ -250,6 +250,7 @@ using namespace qlc;
 extern "C" qlc_status qlc_quantize_e4m3(const void* d_x, qlc_dtype dtype, size_t n, uint8_t* d_codes,
                                         float* d_scales, uint64_t* d_hist, int accumulate, uint32_t* d_status,
                                         qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_quantize_e4m3");
   if (dtype != QLC_DTYPE_F32 && dtype != QLC_DTYPE_BF16) return QLC_ERR_ARG;
   if (n > 0 && (!d_x || !d_codes || !d_scales)) return QLC_ERR_ARG;
   if (!aligned(d_x, 16) || !aligned(d_codes, 16) || !aligned(d_scales, 16) || !aligned(d_hist, 8) ||
@@ -273,6 +274,7 @@ extern "C" qlc_status qlc_quantize_e4m3(const void* d_x, qlc_dtype dtype, size_t
 
 extern "C" qlc_status qlc_dequantize_e4m3(const uint8_t* d_codes, const float* d_scales, size_t n, void* d_out,
                                           qlc_dtype dtype, qlc_stream_t stream) {
+  NvtxRange nvtx_range("qlc_dequantize_e4m3");
   if (dtype != QLC_DTYPE_F32 && dtype != QLC_DTYPE_BF16) return QLC_ERR_ARG;
   if (n > 0 && (!d_codes || !d_scales || !d_out)) return QLC_ERR_ARG;
   if (!aligned(d_codes, 16) || !aligned(d_out, 16) || !aligned(d_scales, 4)) return QLC_ERR_ARG;
