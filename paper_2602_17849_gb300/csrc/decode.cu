@@ -487,15 +487,7 @@ decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
     if (lane == 0) t = atomicAdd(ticket, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= total) break;
-    int sh = 0;
-    {
-      int lo = 0, hi = n_shards - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (item_base[mid] <= t) lo = mid; else hi = mid - 1;
-      }
-      sh = lo;
-    }
+    const int sh = shard_of_warp(item_base, n_shards, t, lane);
     if (sh == bad) continue;
     const qlc_desc dd = descs[sh];
     const uint8_t* in = static_cast<const uint8_t*>(dd.in);

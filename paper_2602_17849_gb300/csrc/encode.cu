@@ -185,17 +185,6 @@ struct EncArgs {
   uint32_t* status;
 };
 
-// Largest s with item_base[s] <= t (the shard holding item t).
-__device__ __forceinline__ int shard_of(const unsigned long long* item_base, int n_shards,
-                                        unsigned long long t) {
-  int lo = 0, hi = n_shards - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (item_base[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // Packing state of one warp within one chunk.  The warp appends 512
 // symbols per step (16 per lane, in lane order) to the chunk's bit stream in a
 // per-warp staging window; completed 16-byte blocks go to the payload, except
@@ -338,26 +327,30 @@ encode_kernel(EncArgs A) {
 
   while (true) {
     __syncthreads();
-    if (tid == 0) {
-      const unsigned long long t = atomicAdd(A.ticket, 1u);
-      s_item = t;
-      if (t < n_items) {
-        if (A.descs) {
-          const int sh = shard_of(A.item_base, A.n_shards, t);
-          const qlc_desc d = A.descs[sh];
-          s_first = A.item_base[sh];
-          s_in = static_cast<const uint8_t*>(d.in);
-          s_n = d.in_bytes;
-          s_lut = d.lut;
-          s_out = static_cast<uint8_t*>(d.out);
-          s_ob = reinterpret_cast<unsigned long long*>(d.out_bytes);
-        } else {
-          s_first = 0;
-          s_in = A.in;
-          s_n = A.n;
-          s_lut = A.lut;
-          s_out = A.out;
-          s_ob = A.out_bytes;
+    if (warp == 0) {  // the next group and, in a batch, its shard
+      unsigned long long t = 0;
+      if (lane == 0) t = atomicAdd(A.ticket, 1u);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      const int sh = A.descs && t < n_items ? shard_of_warp(A.item_base, A.n_shards, t, lane) : 0;
+      if (lane == 0) {
+        s_item = t;
+        if (t < n_items) {
+          if (A.descs) {
+            const qlc_desc d = A.descs[sh];
+            s_first = A.item_base[sh];
+            s_in = static_cast<const uint8_t*>(d.in);
+            s_n = d.in_bytes;
+            s_lut = d.lut;
+            s_out = static_cast<uint8_t*>(d.out);
+            s_ob = reinterpret_cast<unsigned long long*>(d.out_bytes);
+          } else {
+            s_first = 0;
+            s_in = A.in;
+            s_n = A.n;
+            s_lut = A.lut;
+            s_out = A.out;
+            s_ob = A.out_bytes;
+          }
         }
       }
     }

@@ -88,6 +88,26 @@ __device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
   return __uint_as_float(((c & 0x80u) << 24) | ((c & 0x7Fu) << 20)) * 0x1p120f;
 }
 
+// The shard holding work item t of a batch: the largest s < n_shards with
+// item_base[s] <= t (item_base is non-decreasing and item_base[0] = 0, so
+// shards without items are skipped).  Warp-wide: each round the 32 lanes
+// probe 32 evenly spaced entries of the remaining range and the last lane
+// whose entry is <= t narrows it, so 1152 shards take 3 rounds of loads
+// instead of the 11 dependent loads of a binary search.  Every lane returns
+// the same shard.
+__device__ __forceinline__ int shard_of_warp(const unsigned long long* __restrict__ item_base, int n_shards,
+                                             unsigned long long t, int lane) {
+  int lo = 0, hi = n_shards;  // item_base[lo] <= t; the shard lies in [lo, hi)
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) / 32;
+    const int idx = lo + lane * step;
+    const unsigned le = __ballot_sync(0xffffffffu, idx < hi && item_base[idx] <= t);
+    lo += (31 - __clz(le)) * step;  // lane 0 always qualifies
+    hi = min(lo + step, hi);
+  }
+  return lo;
+}
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 
