@@ -225,3 +225,35 @@ def test_full_size_batched_large_compressibility_vs_huffman(qlc):
         assert ent[shared] >= huf[shared] >= code >= container > 0
         assert code - container <= 0.001
     assert got[False][1] >= got[True][1]
+
+
+SMALL_KINDS = ["t4", "gauss", "laplace", "relu_t4", "ffn2"]
+
+
+@pytest.mark.parametrize("n_shards", [1, 33, 3000])
+def test_batch_many_small_shards_with_empty_runs(qlc, n_shards):
+    """Up to 3000 shards of at most 5000 bytes, with runs of empty shards at the
+    start, the end and in between: every shard's item is found (a 32-way
+    search over the item prefix, several rounds at 3000 shards), every shard
+    round-trips, and sampled containers match the oracle."""
+    rng = np.random.default_rng(n_shards)
+    sizes = [int(rng.integers(1, 5000)) if rng.random() < 0.7 else 0 for _ in range(n_shards)]
+    if n_shards > 10:
+        sizes[:4] = [0, 0, 0, 0]
+        sizes[-3:] = [0, 0, 0]
+        sizes[n_shards // 2:n_shards // 2 + 5] = [0] * 5
+        sizes[1] = 777
+    shards = [inputs.make_e4m3(SMALL_KINDS[i % len(SMALL_KINDS)], s, seed=i, device="cuda") if s
+              else torch.zeros(16, dtype=torch.uint8, device="cuda")[:0] for i, s in enumerate(sizes)]
+    b = qlc.Batch(shards, 128)
+    b.encode()
+    b.decode()
+    torch.cuda.synchronize()
+    b.check()
+    for i, s in enumerate(shards):
+        assert torch.equal(b.output(i), s), i
+    cb = _host(b.c_bytes)
+    sample = {0, 1, n_shards - 1, n_shards // 2} | {int(v) for v in rng.integers(0, n_shards, 12)}
+    for i in sorted(i for i in sample if i < n_shards):
+        want = oracle.encode(_host(shards[i]), scheme_id=1, chunk_symbols=128)
+        assert np.array_equal(_host(b.container(i))[: cb[i]], want), i
