@@ -26,16 +26,29 @@ hist_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __re
   flush_cols(hc_sm, hist, tid);
 }
 
-// Rank of symbol s (Section 7): symbols with a larger count, or the same
-// count and a smaller value, come first.  256 threads, one per symbol; no
-// sort, each thread counts the symbols ahead of it.
-__device__ __forceinline__ int rank_of(const unsigned long long* h, int s) {
-  const unsigned long long c = h[s];
+// Rank of a symbol (Section 7): symbols with a larger count, or the same
+// count and a smaller value, come first.  With key(t) = count(t) * 256 +
+// (255 - t), which is unique and orders exactly that way (counts stay below
+// 2^56), the rank of s is the number of keys above key(s): no sort.  Four
+// threads share a symbol (1024 threads per LUT); thread q compares the keys
+// t = 4 i + q, so the four threads of a symbol read four neighbouring keys
+// (different banks), and two shuffles add their counts.
+constexpr int kLutThreads = 1024;
+
+__device__ __forceinline__ void load_keys(const unsigned long long* __restrict__ hist, unsigned long long* key,
+                                          int tid) {
+  if (tid < 256) key[tid] = (hist[tid] << 8) | (unsigned long long)(255 - tid);
+}
+
+// Every thread of the CTA: the rank of symbol tid / 4.
+__device__ __forceinline__ int rank_of(const unsigned long long* key, int tid) {
+  const int s = tid >> 2, q = tid & 3;
+  const unsigned long long k = key[s];
   int r = 0;
-  for (int t = 0; t < 256; t++) {
-    const unsigned long long d = h[t];
-    r += (d > c) | ((d == c) & (t < s));
-  }
+#pragma unroll 16
+  for (int i = 0; i < 64; i++) r += key[4 * i + q] > k;
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
   return r;
 }
 
@@ -56,17 +69,20 @@ __host__ __device__ inline uint32_t lut_entry(const qlc_scheme& sc, int r) {
   return 0;
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kLutThreads)
 lut_kernel(const unsigned long long* __restrict__ hist, qlc_scheme sc, qlc_lut* __restrict__ lut) {
-  __shared__ unsigned long long h[256];
-  const int s = threadIdx.x;
-  h[s] = hist[s];
+  __shared__ unsigned long long key[256];
+  const int tid = threadIdx.x;
+  load_keys(hist, key, tid);
   __syncthreads();
-  const int r = rank_of(h, s);
-  lut->enc[s] = (uint16_t)lut_entry(sc, r);
-  lut->dec[r] = (uint8_t)s;
-  if (s < (int)(sizeof(qlc_scheme) / 4))
-    reinterpret_cast<uint32_t*>(&lut->scheme)[s] = reinterpret_cast<const uint32_t*>(&sc)[s];
+  const int r = rank_of(key, tid);
+  const int s = tid >> 2;
+  if ((tid & 3) == 0) {
+    lut->enc[s] = (uint16_t)lut_entry(sc, r);
+    lut->dec[r] = (uint8_t)s;
+  }
+  if (tid < (int)(sizeof(qlc_scheme) / 4))
+    reinterpret_cast<uint32_t*>(&lut->scheme)[tid] = reinterpret_cast<const uint32_t*>(&sc)[tid];
 }
 
 struct SchemeSet {
@@ -78,19 +94,21 @@ struct SchemeSet {
 // is scored by its payload bits sum_s count[s] * len(rank[s]) and the
 // smallest wins (ties: the earlier candidate).
 // One CTA per histogram: CTA b builds luts[b] from hists[b * 256 ...].
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kLutThreads)
 lut_best_kernel(const unsigned long long* __restrict__ hists, SchemeSet set, qlc_lut* __restrict__ luts) {
-  __shared__ unsigned long long h[256];
-  __shared__ unsigned long long bits[8][8];
+  constexpr int kWarps = kLutThreads / 32;
+  __shared__ unsigned long long key[256];
+  __shared__ unsigned long long bits[8][kWarps];
   const unsigned long long* hist = hists + (size_t)blockIdx.x * 256;
   qlc_lut* lut = luts + blockIdx.x;
-  const int s = threadIdx.x;
-  h[s] = hist[s];
+  const int tid = threadIdx.x;
+  load_keys(hist, key, tid);
   __syncthreads();
-  const int r = rank_of(h, s);
-  const int warp = s >> 5, lane = s & 31;
+  const int r = rank_of(key, tid);
+  const int s = tid >> 2, warp = tid >> 5, lane = tid & 31;
+  const unsigned long long count = key[s] >> 8;
   for (int k = 0; k < set.count; k++) {
-    unsigned long long v = h[s] * (unsigned long long)(lut_entry(set.s[k], r) & 15u);
+    unsigned long long v = (tid & 3) == 0 ? count * (unsigned long long)(lut_entry(set.s[k], r) & 15u) : 0ull;
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) bits[k][warp] = v;
   }
@@ -99,17 +117,19 @@ lut_best_kernel(const unsigned long long* __restrict__ hists, SchemeSet set, qlc
   unsigned long long best_bits = ~0ull;
   for (int k = 0; k < set.count; k++) {
     unsigned long long t = 0;
-    for (int w = 0; w < 8; w++) t += bits[k][w];
+    for (int w = 0; w < kWarps; w++) t += bits[k][w];
     if (t < best_bits) {
       best_bits = t;
       best = k;
     }
   }
   const qlc_scheme& sc = set.s[best];
-  lut->enc[s] = (uint16_t)lut_entry(sc, r);
-  lut->dec[r] = (uint8_t)s;
-  if (s < (int)(sizeof(qlc_scheme) / 4))
-    reinterpret_cast<uint32_t*>(&lut->scheme)[s] = reinterpret_cast<const uint32_t*>(&sc)[s];
+  if ((tid & 3) == 0) {
+    lut->enc[s] = (uint16_t)lut_entry(sc, r);
+    lut->dec[r] = (uint8_t)s;
+  }
+  if (tid < (int)(sizeof(qlc_scheme) / 4))
+    reinterpret_cast<uint32_t*>(&lut->scheme)[tid] = reinterpret_cast<const uint32_t*>(&sc)[tid];
 }
 
 int sm_count() {
@@ -200,7 +220,7 @@ qlc_status qlc_build_lut(const uint64_t* d_hist, const qlc_scheme* h_scheme, qlc
   NvtxRange nvtx_range("qlc_build_lut");
   if (!d_hist || !d_lut || !scheme_valid(h_scheme)) return QLC_ERR_ARG;
   if (!aligned(d_hist, 8) || !aligned(d_lut, 16)) return QLC_ERR_ARG;
-  lut_kernel<<<1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+  lut_kernel<<<1, kLutThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const unsigned long long*>(d_hist), clean_scheme(h_scheme), d_lut);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
@@ -216,7 +236,7 @@ qlc_status qlc_build_lut_best(const uint64_t* d_hist, const qlc_scheme* h_scheme
     if (!scheme_valid(&h_schemes[k])) return QLC_ERR_ARG;
     set.s[k] = clean_scheme(&h_schemes[k]);
   }
-  lut_best_kernel<<<1, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+  lut_best_kernel<<<1, kLutThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const unsigned long long*>(d_hist), set, d_lut);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
@@ -233,7 +253,7 @@ qlc_status qlc_build_lut_batch(const uint64_t* d_hists, int n_luts, const qlc_sc
     if (!scheme_valid(&h_schemes[k])) return QLC_ERR_ARG;
     set.s[k] = clean_scheme(&h_schemes[k]);
   }
-  lut_best_kernel<<<n_luts, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+  lut_best_kernel<<<n_luts, kLutThreads, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
       reinterpret_cast<const unsigned long long*>(d_hists), set, d_luts);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
