@@ -29,26 +29,22 @@ hist_kernel(const uint8_t* __restrict__ in, uint64_t n, unsigned long long* __re
 // Rank of a symbol (Section 7): symbols with a larger count, or the same
 // count and a smaller value, come first.  With key(t) = count(t) * 256 +
 // (255 - t), which is unique and orders exactly that way (counts stay below
-// 2^56), the rank of s is the number of keys above key(s): no sort.  Four
-// threads share a symbol (1024 threads per LUT); thread q compares the keys
-// t = 4 i + q, so the four threads of a symbol read four neighbouring keys
-// (different banks), and two shuffles add their counts.
-constexpr int kLutThreads = 1024;
+// 2^56), the rank of s is the number of keys above key(s): no sort, one
+// comparison per key.  One thread per symbol; all threads read the same key
+// at a time (a broadcast).
+constexpr int kLutThreads = 256;
 
 __device__ __forceinline__ void load_keys(const unsigned long long* __restrict__ hist, unsigned long long* key,
                                           int tid) {
-  if (tid < 256) key[tid] = (hist[tid] << 8) | (unsigned long long)(255 - tid);
+  key[tid] = (hist[tid] << 8) | (unsigned long long)(255 - tid);
 }
 
-// Every thread of the CTA: the rank of symbol tid / 4.
-__device__ __forceinline__ int rank_of(const unsigned long long* key, int tid) {
-  const int s = tid >> 2, q = tid & 3;
+// The rank of symbol s.
+__device__ __forceinline__ int rank_of(const unsigned long long* key, int s) {
   const unsigned long long k = key[s];
   int r = 0;
 #pragma unroll 16
-  for (int i = 0; i < 64; i++) r += key[4 * i + q] > k;
-  r += __shfl_xor_sync(0xffffffffu, r, 1);
-  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  for (int t = 0; t < 256; t++) r += key[t] > k;
   return r;
 }
 
@@ -75,12 +71,10 @@ lut_kernel(const unsigned long long* __restrict__ hist, qlc_scheme sc, qlc_lut* 
   const int tid = threadIdx.x;
   load_keys(hist, key, tid);
   __syncthreads();
-  const int r = rank_of(key, tid);
-  const int s = tid >> 2;
-  if ((tid & 3) == 0) {
-    lut->enc[s] = (uint16_t)lut_entry(sc, r);
-    lut->dec[r] = (uint8_t)s;
-  }
+  const int s = tid;
+  const int r = rank_of(key, s);
+  lut->enc[s] = (uint16_t)lut_entry(sc, r);
+  lut->dec[r] = (uint8_t)s;
   if (tid < (int)(sizeof(qlc_scheme) / 4))
     reinterpret_cast<uint32_t*>(&lut->scheme)[tid] = reinterpret_cast<const uint32_t*>(&sc)[tid];
 }
@@ -104,11 +98,11 @@ lut_best_kernel(const unsigned long long* __restrict__ hists, SchemeSet set, qlc
   const int tid = threadIdx.x;
   load_keys(hist, key, tid);
   __syncthreads();
-  const int r = rank_of(key, tid);
-  const int s = tid >> 2, warp = tid >> 5, lane = tid & 31;
+  const int s = tid, warp = tid >> 5, lane = tid & 31;
+  const int r = rank_of(key, s);
   const unsigned long long count = key[s] >> 8;
   for (int k = 0; k < set.count; k++) {
-    unsigned long long v = (tid & 3) == 0 ? count * (unsigned long long)(lut_entry(set.s[k], r) & 15u) : 0ull;
+    unsigned long long v = count * (unsigned long long)(lut_entry(set.s[k], r) & 15u);
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) bits[k][warp] = v;
   }
@@ -124,10 +118,8 @@ lut_best_kernel(const unsigned long long* __restrict__ hists, SchemeSet set, qlc
     }
   }
   const qlc_scheme& sc = set.s[best];
-  if ((tid & 3) == 0) {
-    lut->enc[s] = (uint16_t)lut_entry(sc, r);
-    lut->dec[r] = (uint8_t)s;
-  }
+  lut->enc[s] = (uint16_t)lut_entry(sc, r);
+  lut->dec[r] = (uint8_t)s;
   if (tid < (int)(sizeof(qlc_scheme) / 4))
     reinterpret_cast<uint32_t*>(&lut->scheme)[tid] = reinterpret_cast<const uint32_t*>(&sc)[tid];
 }
