@@ -109,12 +109,12 @@ plan_kernel(int kind, const qlc_desc* descs, int n_shards, uint32_t cs, BatchWs 
 
 // Each CTA (seven warps, lane-private columns from hist_cols.cuh; two CTAs
 // per SM over the launch, one resident at a time) takes a contiguous run of
-// items.  Its items of one shard are one
-// contiguous byte range, counted in a single streaming pass; the columns are
-// flushed into a shard's histogram when the target histogram changes (never,
-// for one shared histogram).  A CTA's run is at most one item per SM's share
-// of the batch, under 2^32 bytes per shard as long as the batch holds fewer
-// than 2^32 x SMs bytes.
+// items.  Its items of one shard are one contiguous byte range, counted in a
+// single streaming pass; the columns are flushed into a shard's histogram
+// when the target histogram changes (never, for one shared histogram).  A
+// run is 1 / (2 x SMs) of the batch's items, so a lane's counters stay below
+// 2^32 for any batch smaller than 2^32 x 2 x SMs bytes, far above the
+// device's memory.
 __global__ void __launch_bounds__(kHcThreads, 1)
 hist_batch_kernel(const qlc_desc* descs, int n_shards, const unsigned long long* item_base,
                   unsigned long long* hists, int shared) {
