@@ -257,3 +257,30 @@ def test_batch_many_small_shards_with_empty_runs(qlc, n_shards):
     for i in sorted(i for i in sample if i < n_shards):
         want = oracle.encode(_host(shards[i]), scheme_id=1, chunk_symbols=128)
         assert np.array_equal(_host(b.container(i))[: cb[i]], want), i
+
+
+def test_batch_bit_identical_for_every_launch_shape(qlc):
+    """The autotuner's choices change only the launch shape (CTAs per SM for
+    encode and decode) and the chunk size: for a fixed chunk size, every
+    shape gives the same containers and outputs byte for byte, and they are
+    the oracle's."""
+    sizes = [1, 4096, 70_001, 300_000, 0, 1_000_003]
+    shards = [inputs.make_e4m3(("t4", "gauss", "laplace")[i % 3], s, seed=40 + i, device="cuda") if s
+              else torch.zeros(16, dtype=torch.uint8, device="cuda")[:0] for i, s in enumerate(sizes)]
+    ref = None
+    for launch in [(1, 8), (2, 16), (3, 20), (3, 26), (2, 12)]:
+        b = qlc.Batch(shards, 2048, launch=launch)
+        b.encode()
+        b.decode()
+        torch.cuda.synchronize()
+        b.check()
+        cb = _host(b.c_bytes)
+        conts = [_host(b.container(i))[: cb[i]].copy() for i in range(len(shards))]
+        for i, s in enumerate(shards):
+            assert torch.equal(b.output(i), s), (launch, i)
+        if ref is None:
+            ref = conts
+            for i, s in enumerate(shards):
+                assert np.array_equal(conts[i], oracle.encode(_host(s), scheme_id=1, chunk_symbols=2048)), i
+        else:
+            assert all(np.array_equal(a, c) for a, c in zip(ref, conts)), launch
