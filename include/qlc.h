@@ -108,7 +108,11 @@ int qlc_scheme_check(const qlc_scheme *s);
 /* 256-bin byte histogram (Section 4: 8-bit symbols).
  * d_in: n bytes, 16-byte aligned.  d_hist: 256 uint64 counts on the device.
  * accumulate = 0 overwrites d_hist, 1 adds to it (aggregate histograms over
- * shards, as the paper's PMFs are averaged over shards).  Async on stream. */
+ * shards, as the paper's PMFs are averaged over shards).  Async on stream.
+ * The kernel holds 224 KB of shared memory per block (one block per SM); the
+ * first call on a device raises the kernel's shared-memory limit once (a
+ * function attribute, allowed inside stream capture), and QLC_ERR_CUDA
+ * reports a device that cannot provide it. */
 qlc_status qlc_histogram(const uint8_t *d_in, size_t n, uint64_t *d_hist,
                          int accumulate, qlc_stream_t stream);
 
@@ -223,7 +227,7 @@ size_t qlc_batch_workspace_size(int n_shards, uint64_t total_symbols, uint32_t c
 /* Histograms of the shards (Section 4).  shared = 0: d_hists holds
  * n_shards x 256 counts, one histogram per shard; shared = 1: one histogram
  * over all shards (an a-priori LUT per tensor type, Section 7).  Overwrites
- * d_hists.  Uses d_ws.  Async on stream. */
+ * d_hists.  Uses d_ws.  Async on stream.  Shared memory as qlc_histogram. */
 qlc_status qlc_histogram_batch(const qlc_desc *d_descs, int n_shards, uint64_t *d_hists, int shared,
                                void *d_ws, size_t ws_bytes, qlc_stream_t stream);
 
