@@ -151,6 +151,64 @@ def cpu_oracle_roundtrip(x_host, budget_s: float = 12.0, slice_bytes: int = 16 <
     return done, t
 
 
+def _oracle_slice_worker(s):
+    """One oracle round trip of slice s in a worker process (spawned, so it
+    holds no CUDA state); returns the bytes coded."""
+    import numpy as np
+
+    import oracle
+    c = oracle.encode(s, scheme_id=SCHEME, chunk_symbols=CHUNK)
+    st, y, _ = oracle.decode(c)
+    if st != 0 or not np.array_equal(y, s):
+        raise RuntimeError("oracle round trip failed")
+    return int(s.size)
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+class OraclePool:
+    """The oracle on every host core: `cores` spawned worker processes, each
+    coding its own slice (one oracle call per slice, as it stands).  Worker
+    start-up and library loading happen before any timing; a worker that
+    cannot start raises instead of being replaced."""
+
+    def __init__(self, cores: int):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+
+        import numpy as np
+        self.cores = cores
+        self.pool = ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
+        list(self.pool.map(_oracle_slice_worker, [np.zeros(4096, np.uint8)] * cores))
+
+    def run(self, x_host, budget_s: float, slice_bytes: int = 16 << 20, max_bytes=None, start: int = 0):
+        """Consecutive slices of x_host from byte `start` (wrapping around),
+        one per core in flight, until budget_s of wall time or max_bytes
+        submitted; returns (bytes, wall seconds)."""
+        n = x_host.size
+        submitted, done = 0, 0
+
+        def submit():
+            nonlocal submitted
+            off = (start + submitted) % n
+            sl = x_host[off:off + slice_bytes]
+            submitted += sl.size
+            return self.pool.submit(_oracle_slice_worker, sl)
+
+        t0 = time.perf_counter()
+        pending = [submit() for _ in range(self.cores)]
+        while pending:
+            done += pending.pop(0).result()
+            if time.perf_counter() - t0 < budget_s and (max_bytes is None or submitted < max_bytes):
+                pending.append(submit())
+        return done, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.shutdown()
+
+
 def _config(world: int) -> dict:
     """The workload both arms report."""
     return {"workload": WORKLOAD, "shape": [16384, 16384], "n_bytes": N_BYTES,
@@ -169,24 +227,29 @@ def run_reference(args):
     from paper_2602_17849_gb300 import inputs
     x = inputs.make_e4m3("t4", N_BYTES, seed=0).numpy()
     slice_bytes = 16 << 20
-    for _ in range(args.warmup):
-        cpu_oracle_roundtrip(x[:slice_bytes], budget_s=1e9, slice_bytes=slice_bytes, max_bytes=slice_bytes)
-    times = []
+    cores = host_cores()
+    pool = OraclePool(cores)
+    step_bytes = cores * slice_bytes   # one slice per core per step
+    for k in range(args.warmup):
+        pool.run(x, budget_s=0.0, slice_bytes=slice_bytes, max_bytes=step_bytes, start=k * step_bytes)
+    times, done = [], 0
     for k in range(args.steps):
-        off = (k * slice_bytes) % N_BYTES
-        b, t = cpu_oracle_roundtrip(x[off:off + slice_bytes], budget_s=1e9, slice_bytes=slice_bytes,
-                                    max_bytes=slice_bytes)
+        b, t = pool.run(x, budget_s=0.0, slice_bytes=slice_bytes, max_bytes=step_bytes,
+                        start=(args.warmup + k) * step_bytes)
         times.append(t)
+        done += b
+    pool.close()
     tot = sum(times)
-    value = args.steps * slice_bytes / tot / 1e9
-    sample = f"{slice_bytes >> 20} MiB slice of the 256 MiB tensor per step (oracle encode+decode)"
+    value = done / tot / 1e9
+    sample = (f"{cores} x {slice_bytes >> 20} MiB slices of the 256 MiB tensor per step, one per host core "
+              f"(oracle encode+decode)")
     line = {
         "metric": "QLC encode+decode round trip, raw GB/s", "value": value, "unit": "GB/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic", "impl": "reference",
         "config": _config(world),
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -655,11 +718,19 @@ def main():
     if args.serve_seconds > 0:
         line["serving"] = serve_leg(dev, args.serve_seconds)
     if rank == 0 and world == 1 and args.cpu_budget > 0:
+        # the oracle on every host core (spawned workers), and on one core
         xh = x.cpu().numpy()
-        b, s = cpu_oracle_roundtrip(xh, budget_s=args.cpu_budget)
-        line["cpu_baseline"] = {"value": b / s / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{b >> 20} MiB of the tensor in consecutive 16 MiB slices "
-                                          f"(wrapping around), oracle encode+decode, {s:.1f} s"}
+        cores = host_cores()
+        pool = OraclePool(cores)
+        b, s = pool.run(xh, budget_s=args.cpu_budget * 2 / 3)
+        pool.close()
+        b1, s1 = cpu_oracle_roundtrip(xh, budget_s=args.cpu_budget / 3)
+        line["cpu_baseline"] = {"value": b / s / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{b >> 20} MiB of the tensor in 16 MiB slices (wrapping around), "
+                                          f"one oracle encode+decode per slice, {cores} worker processes, "
+                                          f"{s:.1f} s wall",
+                                "one_core": {"value": b1 / s1 / 1e9, "cores": 1,
+                                             "sample": f"{b1 >> 20} MiB in consecutive 16 MiB slices, {s1:.1f} s"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
