@@ -380,7 +380,7 @@ def large_leg(dev, steps: int, warmup: int, peak: float):
     return out
 
 
-def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152):
+def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152, shape=None):
     """The batched workload (1152 shards, 64 KiB - 16 MiB, t4 / gauss / laplace,
     per-shard LUTs): one CUDA graph per direction with the autotuned launch
     shape, against per-tensor launches of the plain kernels (eager, and the
@@ -391,7 +391,10 @@ def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152)
     arena, shards = inputs.cfg3_batch(dev, n_shards)
     torch.cuda.empty_cache()
     total = sum(x.numel() for x in shards)
-    cfg = autotune.tune(shards)
+    if shape is None:
+        cfg = autotune.tune(shards)
+    else:  # a fixed launch shape (profiling captures): no tuning launches
+        cfg = dict(zip(("chunk_symbols", "encode_ctas_per_sm", "decode_ctas_per_sm"), shape))
     cs = cfg["chunk_symbols"]
     b = qlc.Batch(shards, cs, launch=(cfg["encode_ctas_per_sm"], cfg["decode_ctas_per_sm"]))
     b.capture()
@@ -591,6 +594,9 @@ def main():
                     help="elements in the fused leg (fewer only for profiling captures)")
     ap.add_argument("--batched-shards", type=int, default=1152,
                     help="shards in the batched leg (fewer only for profiling captures)")
+    ap.add_argument("--batched-shape", default=None,
+                    help="chunk,encode_ctas_per_sm,decode_ctas_per_sm for the batched leg instead of "
+                         "autotuning (profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -710,7 +716,8 @@ def main():
         "clocks": clk.summary(),
     }
     if not args.no_batched:
-        line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.batched_shards)
+        shape = tuple(int(v) for v in args.batched_shape.split(",")) if args.batched_shape else None
+        line["batched"] = batched_leg(dev, max(3, args.steps // 2), args.warmup, peak, args.batched_shards, shape)
     if not args.no_large:
         line["batched_large"] = large_leg(dev, max(3, args.steps // 2), args.warmup, peak)
     if not args.no_fused:
