@@ -34,16 +34,13 @@
  *      the smallest fp32 subnormal) has codes 0x00.  The codec
  *      itself never depends on this; only the fused quantise / dequantise
  *      entry points and the input generator do.
- *   R6 Stream layout: the paper decodes one serial stream; the container's
- *      chunks and their two streams (below) only decide where each codeword
- *      sits, never which bits it has.
  *   R4 Scheme family: areas with fewer than 8 suffix bits hold exactly
  *      2^bits ranks; areas with 8 suffix bits hold 1..256; the counts sum to
  *      256 and suffix widths never decrease from area to area.
  *
- * Container v2 (not in the paper; all integers little-endian):
+ * Container v1 (not in the paper; all integers little-endian):
  *     0  char[4]  magic "QLC1"
- *     4  u16      version = 2
+ *     4  u16      version = 1
  *     6  u8       scheme id (1 = Table 1, 2 = Table 2, 0 = other)
  *     7  u8       flags = 0
  *     8  u64      n, number of symbols
@@ -57,19 +54,10 @@
  *   320  u64[G]   group_off: payload byte offset of each group of 32 chunks
  *        u16[n_chunks] chunk_bits: bits of each chunk's codewords
  *        zero pad to a multiple of 16 bytes; the payload starts there (P)
- *     P  payload: group g holds chunks 32g..32g+31, their bit strings back
- *        to back (bit-contiguous across chunk borders), zero-padded to a
+ *     P  payload: group g holds chunks 32g..32g+31, their codewords back to
+ *        back (bit-contiguous across chunk borders), zero-padded to a
  *        multiple of 16 bytes.  group_off[0] = 0 and each next group starts
  *        where the padded previous one ends; payload bytes = their sum.
- *   Two streams per chunk (R6).  A chunk of m symbols x_0..x_{m-1} splits at
- *   h = min(m, 32 * ceil(m / 64)): its bit string is F followed by the
- *   reverse of B, where F = codewords of x_0..x_{h-1} and B = codewords of
- *   x_h..x_{m-1}, each written most significant bit first.  Read forward from
- *   the chunk's first bit, it gives x_0..x_{h-1}; read backward from its
- *   last bit, it gives x_h, x_{h+1}, ..., x_{m-1}; the two readings meet
- *   exactly, and chunk_bits = |F| + |B|.  Both starts follow from the index
- *   with no further bytes, so a chunk can be decoded as two independent
- *   serial streams.
  *
  * Parity status: every function here is pinned by tests under tests/ (see
  * the file headers there); the paper's own compressibility figures (13.9%,
@@ -228,12 +216,6 @@ static int chunk_symbols_ok(uint32_t cs) {
   return cs >= 128 && cs <= 4096 && cs % 128 == 0;
 }
 
-/* R6: how many of a chunk's m symbols its forward stream carries. */
-static uint64_t forward_symbols(uint64_t m) {
-  uint64_t h = 32 * ((m + 63) / 64);
-  return h < m ? h : m;
-}
-
 static uint64_t payload_start(uint64_t n_chunks) {
   uint64_t n_groups = (n_chunks + CHUNKS_PER_GROUP - 1) / CHUNKS_PER_GROUP;
   return align16(INDEX_OFF + 8 * n_groups + 2 * n_chunks);
@@ -303,19 +285,10 @@ int oracle_encode(const uint8_t *x, uint64_t n, const uint16_t area_n[8],
       uint64_t start = pos;
       uint64_t first = c * chunk_symbols;
       uint64_t last = first + chunk_symbols < n ? first + chunk_symbols : n;
-      uint64_t mid = first + forward_symbols(last - first);
-      /* F: the first h codewords, each most significant bit first */
-      for (uint64_t i = first; i < mid; i++) {
+      for (uint64_t i = first; i < last; i++) {
         uint32_t code = enc_code[x[i]];
         int len = enc_len[x[i]];
         for (int k = len - 1; k >= 0; k--) put_bit(payload, pos++, (code >> k) & 1u);
-      }
-      /* reverse(B): the remaining codewords from the last one back, each
-       * least significant bit first */
-      for (uint64_t i = last; i > mid; i--) {
-        uint32_t code = enc_code[x[i - 1]];
-        int len = enc_len[x[i - 1]];
-        for (int k = 0; k < len; k++) put_bit(payload, pos++, (code >> k) & 1u);
       }
       put_le(out + INDEX_OFF + 8 * n_groups + 2 * c, pos - start, 2);
     }
@@ -323,7 +296,7 @@ int oracle_encode(const uint8_t *x, uint64_t n, const uint16_t area_n[8],
   }
 
   memcpy(out, "QLC1", 4);
-  put_le(out + 4, 2, 2);
+  put_le(out + 4, 1, 2);
   out[6] = (uint8_t)scheme_id;
   out[7] = 0;
   put_le(out + 8, n, 8);
@@ -344,7 +317,7 @@ int oracle_decode(const uint8_t *c, uint64_t c_bytes, uint8_t *out,
                   uint64_t cap, uint64_t *n_out) {
   if (c_bytes < INDEX_OFF) return ORACLE_ERR_CORRUPT;
   if (memcmp(c, "QLC1", 4) != 0) return ORACLE_ERR_CORRUPT;
-  if (get_le(c + 4, 2) != 2 || c[7] != 0 || get_le(c + 56, 8) != 0)
+  if (get_le(c + 4, 2) != 1 || c[7] != 0 || get_le(c + 56, 8) != 0)
     return ORACLE_ERR_CORRUPT;
   uint16_t area_n[8];
   uint8_t area_bits[8];
@@ -379,29 +352,22 @@ int oracle_decode(const uint8_t *c, uint64_t c_bytes, uint8_t *out,
     for (uint64_t ch = g * CHUNKS_PER_GROUP;
          ch < n_chunks && ch < (g + 1) * CHUNKS_PER_GROUP; ch++) {
       uint64_t cbits = get_le(c + INDEX_OFF + 8 * n_groups + 2 * ch, 2);
+      uint64_t start = pos;
       uint64_t first = ch * cs;
       uint64_t last = first + cs < n ? first + cs : n;
-      uint64_t mid = first + forward_symbols(last - first);
-      /* R6: x_first.. forward from the chunk's first bit, x_mid.. backward
-       * from its last bit (pb is one past the next bit to read) */
-      uint64_t pf = pos, pb = pos + cbits;
       for (uint64_t i = first; i < last; i++) {
-        int fwd = i < mid;
         /* Section 7: the area code gives the suffix length ... */
         unsigned area = 0;
-        for (int k = 0; k < 3; k++)
-          area = (area << 1) | (unsigned)get_bit(payload, payload_bytes, fwd ? pf++ : --pb);
+        for (int k = 0; k < 3; k++) area = (area << 1) | (unsigned)get_bit(payload, payload_bytes, pos++);
         unsigned suffix = 0;
         for (int k = 0; k < area_bits[area]; k++)
-          suffix = (suffix << 1) | (unsigned)get_bit(payload, payload_bytes, fwd ? pf++ : --pb);
+          suffix = (suffix << 1) | (unsigned)get_bit(payload, payload_bytes, pos++);
         /* ... then the area offset is added (R1: 0 for 8 suffix bits) and
          * the decoder LUT maps the rank back to the symbol. */
         unsigned rank = area_bits[area] == 8 ? suffix : base[area] + suffix;
         out[i] = dec[rank];
       }
-      /* the two readings must use the chunk's bits exactly, and not overlap */
-      if (pf != pb) return ORACLE_ERR_CORRUPT;
-      pos += cbits;
+      if (pos - start != cbits) return ORACLE_ERR_CORRUPT;
     }
     expect_off = align16((pos + 7) / 8);
   }

@@ -8,7 +8,7 @@
  *
  * Every function follows the paper (arXiv 2602.17849, "Quad Length Codes for
  * Lossless Compression of e4m3") and, for the byte layout the paper leaves
- * open, the container-v2 layout written out in the header comment of
+ * open, the container-v1 layout written out in the header comment of
  * qlc_oracle.c.  Parity status of each function is stated there too.
  */
 #ifndef QLC_ORACLE_H
@@ -51,7 +51,7 @@ int oracle_codeword(const uint16_t area_n[8], const uint8_t area_bits[8],
 int oracle_decode_codeword(const uint16_t area_n[8], const uint8_t area_bits[8],
                            uint32_t code, int len);
 
-/* Container v2: bytes needed in the worst case (11 bits per symbol). */
+/* Container v1: bytes needed in the worst case (11 bits per symbol). */
 uint64_t oracle_container_bound(uint64_t n, uint32_t chunk_symbols);
 
 /* Encode x[0..n) into a container.  sym_of_rank is the decoder LUT

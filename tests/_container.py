@@ -1,7 +1,6 @@
-"""Container-v2 parsing for tests, written from the documented byte layout
+"""Container-v1 parsing for tests, written from the documented byte layout
 (header 64 B, decoder LUT 256 B, u64 group offsets, u16 chunk bit counts,
-zero pad to 16 B, payload; each chunk's second half stored bit-reversed at
-the chunk's end).  Independent of both the oracle and the CUDA path."""
+zero pad to 16 B, payload).  Independent of both the oracle and the CUDA path."""
 import struct
 
 import numpy as np
@@ -38,23 +37,3 @@ def bits_to_bytes(bitstring):
     nbytes = align16((len(bitstring) + 7) // 8)
     s = bitstring + "0" * (nbytes * 8 - len(bitstring))
     return bytes(int(s[i:i + 8], 2) for i in range(0, len(s), 8))
-
-
-def forward_symbols(m):
-    """Symbols of an m-symbol chunk carried by its forward stream:
-    min(m, 32 * ceil(m / 64)); the rest are stored reversed at the chunk's end."""
-    return min(m, 32 * (-(-m // 64)))
-
-
-def chunk_bit_strings(p):
-    """Each chunk's bits as a '0'/'1' string, located by the group offsets and
-    the chunk bit counts of a parsed container."""
-    bits = "".join(format(v, "08b") for v in p["payload"])
-    out = []
-    for g in range(p["n_groups"]):
-        pos = int(p["group_off"][g]) * 8
-        for c in range(32 * g, min(32 * g + 32, p["n_chunks"])):
-            nb = int(p["chunk_bits"][c])
-            out.append(bits[pos:pos + nb])
-            pos += nb
-    return out

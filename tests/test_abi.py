@@ -97,4 +97,4 @@ def test_peek_header_on_oracle_container(qlc):
 def test_status_strings(qlc):
     assert qlc.status_string(0) == "ok"
     assert "corrupt" in qlc.status_string(3)
-    assert qlc.qlc_version() == 2
+    assert qlc.qlc_version() == 1

