@@ -20,7 +20,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache
 
 CHUNKS = (2048, 4096)
 ENC_CTAS = (2, 3)
-DEC_CTAS = (16, 20, 26)
+DEC_CTAS = (12, 16, 20)
 
 
 def _key(total: int, n_shards: int) -> str:

@@ -3,25 +3,30 @@
 // One warp per group of 32 chunks, one lane per chunk: the codes are not
 // self-synchronising, so each lane starts at its chunk's bit offset (group
 // offset + exclusive scan of the group's chunk_bits) and decodes its chunk
-// serially.  Per symbol: the top 3 bits of a 64-bit bit buffer are the area
-// code; the code length 3 + bits[area] comes from a byte permute of two
-// registers (no memory access on the serial path); the whole codeword (area
-// code and suffix, right-aligned) indexes a 2048-entry code -> symbol table in
-// shared memory built from the LUT and the area table.  The rank is never
-// formed explicitly: for every code of every area the table holds
-// dec[offset + suffix] (offset 0 for 8-bit areas), exactly the paper's rule.
-// Input: each lane's chunk bytes stream through a 128-byte shared-memory ring
-// filled by cp.async; the buffer is refilled one word per two symbols under
-// predication, so lanes never diverge.  Output: 16 symbols per shared store
-// into a swizzled 32 x 32-byte tile; every 32 symbols the warp writes the tile
-// out, one 32-byte segment per chunk.
+// serially.  Per symbol: the top 3 bits of a 32-bit window are the area code;
+// the code length 3 + bits[area] comes from a byte permute of two registers
+// (no memory access); the whole codeword (area code and suffix, right-aligned)
+// indexes a 2048-entry code -> symbol table in shared memory built from the
+// LUT and the area table.  The rank is never formed explicitly: for every code
+// of every area the table holds dec[offset + suffix] (offset 0 for 8-bit
+// areas), exactly the paper's rule.
+// Input: each lane's bytes arrive by cp.async in 16-byte vectors into a
+// staging ring, and once per block of 32 symbols the lane moves the vectors it
+// will need next, byte-swapped, into its column of a word ring (word k of lane
+// l in bank l, so the lanes' reads never collide).  The lane decodes from a
+// 64-bit register buffer: two symbols per round from the 32-bit window at its
+// bit position (one funnel shift); when the position crosses a word the
+// buffer moves up and the next word comes from the ring, read one word ahead
+// of its use so that no memory access lies on the round-to-round chain.
+// Output: each lane writes its 32 symbols of a block with one 32-byte
+// streaming store.
 #include <cuda_bf16.h>
 
 #include "qlc_common.cuh"
 
 namespace qlc {
 
-constexpr int kDecCtasPerSm = 26;  // 26 x (7.4 KB + 1 KB reserved) fits in 228 KB
+constexpr int kDecCtasPerSm = 20;  // 20 x (8.3 KB + 1 KB reserved); at 24 the register cap (80) spills
 
 struct DecHeader {
   uint64_t n, payload_bytes, P, n_chunks, n_groups;
@@ -93,10 +98,10 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-constexpr uint32_t kBlk = 32;       // symbols per lane between output flushes
-constexpr uint32_t kRingVec = 8;    // 16-byte vectors in each lane's input ring (128 B)
+constexpr uint32_t kBlk = 32;       // symbols per lane per block
+constexpr uint32_t kStageVec = 8;   // 16-byte vectors staged per lane (128 B of its stream)
+constexpr uint32_t kColRows = 16;   // words in each lane's column ring
 
-// (hi * 8) >> 32 + c, i.e. (hi >> 29) + c, on the multiply-add pipe.
 __device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
   uint32_t d;
   asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
@@ -114,64 +119,109 @@ __device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
   asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
 }
-// 0x80000000 >> s with PTX semantics (0 for s >= 32).
-__device__ __forceinline__ uint32_t top_bit_shr(uint32_t s) {
-  uint32_t d;
-  asm("shr.b32 %0, %1, %2;" : "=r"(d) : "r"(0x80000000u), "r"(s));
-  return d;
-}
-__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-  return v;
-}
 
+// Shared memory of one decoding warp (one CTA): the lanes' staging ring and
+// column ring, and the code table.
+struct DecShared {
+  uint32_t col[kColRows][32];  // word k of lane l at col[k % 16][l]
+  uint4 stage[kStageVec][32];  // vector v of lane l at stage[v % 8][l]
+  uint8_t T[2048];                // code -> symbol
+  __align__(16) uint8_t dec[256];
+  uint32_t seen[8];
+};
 
-// Per-lane decoder state.  Input: the lane's chunk bytes are copied 16 bytes
-// at a time (cp.async) into a 128-byte ring in shared memory, ahead of use.
-// Bits: a 64-bit buffer (hi:lo) of valid bits, most significant first, with
-// nb1 = (valid bits - 1).  Two symbols (at most 2 x 11 bits) are decoded per
-// round with no branch; then one 32-bit word is inserted, under predication,
-// when at most 32 bits are left, which keeps at least 32 valid bits at the
-// start of every round.
+// A lane's bit stream, positions group-relative.  The stream's words j and
+// j + 1 sit in a 64-bit buffer (hi:lo, most significant bit first) and word
+// j + 2 in nxt, where j = p / 32; the window at bit p is one funnel shift of
+// the buffer.  When a round crosses into the next word the buffer moves up
+// by one word and word j + 3 is read from the column ring, so no memory
+// access lies on the chain from one round to the next.
 struct LaneDec {
-  uint32_t hi, lo;
-  uint32_t nb1;
-  uint32_t rpb;  // byte offset (group-relative) of the next word to insert
-  uint32_t nxt;  // that word, already read from the ring
-  uint32_t fv;   // next 16-byte vector to fetch (group-relative)
-  uint32_t vend; // vectors in the group
-  const uint4* gp;
-  uint32_t ring_s;  // shared address of this lane's ring (128-byte aligned)
+  uint32_t p;      // bit position of the next codeword
+  uint32_t hi, lo, nxt;
+  uint32_t tv;     // next vector to move from the staging ring to the column ring
+  uint32_t fv;     // next vector to fetch
+  uint32_t vend;   // vectors of this stream in the group
+  const uint4* gp; // the group's payload
+  uint32_t lane4;      // byte offset of col[0][lane] in the column ring
+  uint32_t col_s;      // shared address of col[0][lane]
+  uint32_t stage_s;    // shared address of stage[0][lane]
 
-  // Fetch vectors up to the ring's capacity past the read position, never
-  // past the group end, and commit them as one cp.async group.
-  __device__ __forceinline__ void fetch() {
-    const uint32_t want = min((rpb >> 4) + kRingVec, vend);
-    for (; fv < want; fv++) cp_async16(ring_s + (fv % kRingVec) * 16, gp + fv);
-    cp_async_commit();
-  }
-  // The same top-up between blocks, as three predicated copies with no
-  // branch: a block of kBlk symbols consumes at most kBlk * 11 bits = 44
-  // bytes, so the read position, and with it `want`, moves by at most three
-  // 16-byte vectors per block.
-  __device__ __forceinline__ void fetch3() {
-    const uint32_t want = min((rpb >> 4) + kRingVec, vend);
+  // Fetches (cp.async, 16 bytes each) vector fv into its staging slot when
+  // fv < want, k times, with no branch; the caller commits the group.
+  template <int k>
+  __device__ __forceinline__ void fetch(uint32_t want) {
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-      const uint32_t p = fv < want;
+    for (int i = 0; i < k; i++) {
+      const uint32_t q = fv < want;
       asm volatile(
           "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q cp.async.cg.shared.global [%0], [%1], 16;\n\t}" ::"r"(
-              ring_s + (fv % kRingVec) * 16),
-          "l"(gp + fv), "r"(p)
+              stage_s + (fv % kStageVec) * 512),
+          "l"(gp + fv), "r"(q)
           : "memory");
-      fv += p;
+      fv += q;
     }
+  }
+  // Moves vector tv from the staging ring to the column ring (byte-swapped,
+  // so each word reads most significant bit first) when its first word is
+  // at most `need` and it exists.
+  __device__ __forceinline__ void move(uint32_t need) {
+    const uint32_t q = (tv * 4 <= need) & (tv < vend);
+    const uint32_t src = stage_s + (tv % kStageVec) * 512;
+    const uint32_t dst = col_s + (tv % 4) * 512;
+      asm volatile(
+          "{\n\t.reg .pred q;\n\t.reg .b32 a, b, c, d;\n\t"
+          "setp.ne.u32 q, %2, 0;\n\t"
+          "@q ld.shared.v4.u32 {a, b, c, d}, [%0];\n\t"
+          "prmt.b32 a, a, 0, 0x0123;\n\t"
+          "prmt.b32 b, b, 0, 0x0123;\n\t"
+          "prmt.b32 c, c, 0, 0x0123;\n\t"
+          "prmt.b32 d, d, 0, 0x0123;\n\t"
+          "@q st.shared.u32 [%1], a;\n\t"
+          "@q st.shared.u32 [%1+128], b;\n\t"
+          "@q st.shared.u32 [%1+256], c;\n\t"
+          "@q st.shared.u32 [%1+384], d;\n\t"
+          "}" ::"r"(src),
+          "r"(dst), "r"(q)
+          : "memory");
+    tv += q;
+  }
+  __device__ __forceinline__ uint32_t ring(const DecShared& sm, uint32_t k) const {
+    return *reinterpret_cast<const uint32_t*>(reinterpret_cast<const uint8_t*>(sm.col) + (((k << 7) & 0x780u) | lane4));
+  }
+  // Set-up at bit S of the group: fill the staging ring, wait for it, move
+  // the words the first block can read, load the buffer, refill.  Words
+  // j .. j + 2 (at most two vectors) go to the buffer before the rest is
+  // moved: the ring holds 16 words, and word j + 16 shares word j's row.
+  __device__ __forceinline__ void start(const DecShared& sm, uint32_t S) {
+    p = S;
+    tv = fv = min(S >> 7, vend);
+    fetch<kStageVec>(min(tv + kStageVec, vend));
+    cp_async_commit();
+    cp_async_wait<0>();
+    const uint32_t j = S >> 5;
+    move(j + 2);
+    move(j + 2);
+    hi = ring(sm, j);
+    lo = ring(sm, j + 1);
+    nxt = ring(sm, j + 2);
+#pragma unroll
+    for (int i = 0; i < 3; i++) move(j + 13);
+    fetch<5>(min(tv + kStageVec, vend));
     cp_async_commit();
   }
-  __device__ __forceinline__ uint32_t ring_word(uint32_t byte_off) const {
-    // ring_s is 128-byte aligned, so OR places the offset inside the ring
-    return bswap32(ld_shared_u32(ring_s | (byte_off & (kRingVec * 16 - 1))));
+  // Before each block of at most 32 symbols (at most 352 bits, so the ring
+  // is read up to word p/32 + 13): move up to three vectors (the position
+  // moved at most 11 words since the last block) and refetch as many.
+  // Vectors moved now were fetched two blocks ago at the latest, so waiting
+  // for all but the latest cp.async group suffices.
+  __device__ __forceinline__ void advance() {
+    cp_async_wait<1>();
+    const uint32_t need = (p >> 5) + 13;
+#pragma unroll
+    for (int i = 0; i < 3; i++) move(need);
+    fetch<3>(min(tv + kStageVec, vend));
+    cp_async_commit();
   }
   // Code length of the codeword at the top of x (Section 7: the area code,
   // i.e. the top 3 bits, fixes it): a byte permute of two registers; the
@@ -179,52 +229,35 @@ struct LaneDec {
   __device__ __forceinline__ static uint32_t code_len(uint32_t x, uint32_t len_lo, uint32_t len_hi) {
     return prmt(len_lo, len_hi, mad_hi(x, 8u, 0x8880u));
   }
-  // Insert the next word below the valid bits when at most 32 remain:
-  // q = 2^(32 - valid), or 0 when no word is due, so the insertion is two
-  // multiply-adds with no select.
-  __device__ __forceinline__ void refill() {
-    const uint32_t q = top_bit_shr(nb1);
-    hi = mad_hi(nxt, q, hi);  // nxt >> valid
-    lo = mad_lo(nxt, q, lo);  // nxt << (32 - valid)
-    if (nb1 < 32) {
-      nb1 += 32;
-      rpb += 4;
-      nxt = ring_word(rpb);
+  // Advances the position to pn (less than 32 bits on): when it crosses into
+  // the next word the buffer moves up a word and the word after nxt is read.
+  __device__ __forceinline__ void step_to(const DecShared& sm, uint32_t pn) {
+    if ((pn ^ p) & 32u) {
+      hi = lo;
+      lo = nxt;
+      nxt = ring(sm, (pn >> 5) + 2);
     }
+    p = pn;
   }
-  // Two symbols (at most 22 bits) from the top of the buffer, packed as
-  // s0 | s1 << 8; the buffer advances once by both lengths.
-  __device__ __forceinline__ uint32_t round2(const uint8_t* T, uint32_t len_lo, uint32_t len_hi) {
-    const uint32_t la = code_len(hi, len_lo, len_hi);
-    const uint32_t a = T[__funnelshift_l(hi, 0u, la)];
-    const uint32_t h1 = __funnelshift_l(lo, hi, la);
-    const uint32_t lb = code_len(h1, len_lo, len_hi);
-    const uint32_t b = T[__funnelshift_l(h1, 0u, lb)];
-    const uint32_t lab = la + lb;
-    hi = __funnelshift_l(lo, hi, lab);
-    lo <<= lab;
-    nb1 -= lab;
-    refill();
+  // Two symbols (at most 22 bits) from the window, packed as s0 | s1 << 8.
+  __device__ __forceinline__ uint32_t round2(const DecShared& sm, uint32_t len_lo, uint32_t len_hi) {
+    const uint32_t x = __funnelshift_l(lo, hi, p);
+    const uint32_t la = code_len(x, len_lo, len_hi);
+    const uint32_t a = sm.T[__funnelshift_l(x, 0u, la)];
+    const uint32_t x2 = x << la;
+    const uint32_t lb = code_len(x2, len_lo, len_hi);
+    const uint32_t b = sm.T[__funnelshift_l(x2, 0u, lb)];
+    step_to(sm, p + la + lb);
     return mad_lo(b, 256u, a);
   }
-  // One symbol with a refill (ragged chunk ends only).
-  __device__ __forceinline__ uint32_t round1(const uint8_t* T, uint32_t len_lo, uint32_t len_hi) {
-    const uint32_t la = code_len(hi, len_lo, len_hi);
-    const uint32_t a = T[__funnelshift_l(hi, 0u, la)];
-    hi = __funnelshift_l(lo, hi, la);
-    lo <<= la;
-    nb1 -= la;
-    refill();
+  // One symbol (ragged chunk ends only).
+  __device__ __forceinline__ uint32_t round1(const DecShared& sm, uint32_t len_lo, uint32_t len_hi) {
+    const uint32_t x = __funnelshift_l(lo, hi, p);
+    const uint32_t la = code_len(x, len_lo, len_hi);
+    const uint32_t a = sm.T[__funnelshift_l(x, 0u, la)];
+    step_to(sm, p + la);
     return a;
   }
-};
-
-struct DecShared {
-  uint8_t T[2048];
-  __align__(128) uint4 ring[32 * kRingVec];
-  __align__(16) uint4 tile[32 * (kBlk / 16)];
-  __align__(16) uint8_t dec[256];
-  uint32_t seen[8];
 };
 
 // code -> symbol table: every code (i << bits[i]) | s of every area i maps to
@@ -246,12 +279,19 @@ __device__ void build_table(const uint8_t* in, DecShared& sm, int lane) {
 // block-32 dequantised values (value(code) * scale, fp32 or rounded to bf16).
 constexpr int kOutCodes = -1;
 
-// Streaming 16-byte store of decoded symbols when pred (a predicated store).
-__device__ __forceinline__ void put16_if(uint8_t* dst, uint4 v, bool pred) {
-  asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};\n\t}" ::"l"(dst),
-      "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"((uint32_t)pred)
-      : "memory");
+// Streaming 32-byte store (dst 32-byte aligned) or two 16-byte stores.
+__device__ __forceinline__ void st_cs_32(uint8_t* dst, const uint32_t w[8], bool aligned32) {
+  if (aligned32) {
+    asm volatile("st.global.cs.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst), "r"(w[0]), "r"(w[1]),
+                 "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+  } else {
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(dst), "r"(w[0]), "r"(w[1]), "r"(w[2]), "r"(w[3])
+                 : "memory");
+    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(dst + 16), "r"(w[4]), "r"(w[5]), "r"(w[6]),
+                 "r"(w[7])
+                 : "memory");
+  }
 }
 
 // Sixteen decoded symbols v of one chunk, starting at symbol index i of the
@@ -304,134 +344,89 @@ __device__ __forceinline__ void put_tail(void* out, const float* scales, uint64_
   }
 }
 
+// Thirty-two decoded symbols w of one chunk, starting at symbol index i of
+// the tensor (a multiple of 32), to their destination.
+template <int kOut>
+__device__ __forceinline__ void put32(void* out, const float* scales, uint64_t i, const uint32_t w[8],
+                                      bool aligned32) {
+  if (kOut == kOutCodes) {
+    st_cs_32(static_cast<uint8_t*>(out) + i, w, aligned32);
+  } else {
+    put16<kOut>(out, scales, i, make_uint4(w[0], w[1], w[2], w[3]));
+    put16<kOut>(out, scales, i + 16, make_uint4(w[4], w[5], w[6], w[7]));
+  }
+}
+
+// One decoded symbol s at index i of the tensor (ragged chunk ends).
+template <int kOut>
+__device__ __forceinline__ void put1(void* out, const float* scales, uint64_t i, uint32_t s) {
+  const uint8_t b = (uint8_t)s;
+  put_tail<kOut>(out, scales, i, &b, 1);
+}
+
 // Decodes group g of a validated container (one warp; lane = chunk).
 template <int kOut>
-__device__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in, void* __restrict__ out,
+__device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in, void* __restrict__ out,
                              const float* __restrict__ scales, uint64_t g, DecShared& sm, LaneDec& d,
-                             uint32_t* status, int lane) {
+                             uint32_t* status, int lane, bool aligned32) {
   const unsigned long long* group_off = reinterpret_cast<const unsigned long long*>(in + kIndexOff);
   const uint16_t* chunk_bits = reinterpret_cast<const uint16_t*>(in + kIndexOff + 8 * h.n_groups);
   const uint4* vbase = reinterpret_cast<const uint4*>(in + h.P);
   const uint32_t cs = h.cs;
   const uint32_t len_lo = h.len_lo, len_hi = h.len_hi;
-  const uint8_t* s_T = sm.T;
-  uint4* s_tile = sm.tile;
-  do {
-    const uint64_t c = g * kGroupChunks + lane;
-    const bool exists = c < h.n_chunks;
-    const uint32_t nsym = exists ? (uint32_t)min((uint64_t)cs, h.n - c * cs) : 0u;
-    const uint32_t bits = exists ? chunk_bits[c] : 0u;
-    uint32_t incl = bits;
+  const uint64_t c = g * kGroupChunks + lane;
+  const bool exists = c < h.n_chunks;
+  const uint32_t nsym = exists ? (uint32_t)min((uint64_t)cs, h.n - c * cs) : 0u;
+  const uint32_t bits = exists ? chunk_bits[c] : 0u;
+  uint32_t incl = bits;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  const uint32_t gbits = __shfl_sync(0xffffffffu, incl, 31);
+  const uint64_t goff = group_off[g];
+  const uint64_t gnext = g + 1 < h.n_groups ? group_off[g + 1] : h.payload_bytes;
+  const bool group_ok = (g != 0 || goff == 0) && (goff & 15u) == 0 && goff <= gnext &&
+                        gnext <= h.payload_bytes && gnext - goff == align16((gbits + 7u) / 8u);
+  if (!group_ok) {
+    if (lane == 0) set_status(status, QLC_ERR_CORRUPT);
+    return;
+  }
+  // lane start bit (group-relative) and ring set-up
+  const uint32_t S = incl - bits;
+  d.gp = vbase + goff / 16;
+  d.vend = (uint32_t)((gnext - goff) / 16);
+  d.start(sm, S);
+  const uint64_t i_chunk = c * cs;  // the chunk's first symbol
+  const uint32_t nmax = __reduce_max_sync(0xffffffffu, nsym);
+  for (uint32_t i0 = 0; i0 < nmax; i0 += kBlk) {
+    d.advance();
+    const uint32_t cnt = nsym > i0 ? min(kBlk, nsym - i0) : 0u;
+    if (cnt == kBlk) {
+      uint32_t w[8];
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const uint32_t p0 = d.round2(sm, len_lo, len_hi);
+        const uint32_t p1 = d.round2(sm, len_lo, len_hi);
+        w[j] = __byte_perm(p0, p1, 0x5410);
+      }
+      put32<kOut>(out, scales, i_chunk + i0, w, aligned32);
+    } else {
+      for (uint32_t k = 0; k < cnt; k++) put1<kOut>(out, scales, i_chunk + i0 + k, d.round1(sm, len_lo, len_hi));
     }
-    const uint32_t gbits = __shfl_sync(0xffffffffu, incl, 31);
-    const uint64_t goff = group_off[g];
-    const uint64_t gnext = g + 1 < h.n_groups ? group_off[g + 1] : h.payload_bytes;
-    const bool group_ok = (g != 0 || goff == 0) && (goff & 15u) == 0 && goff <= gnext &&
-                          gnext <= h.payload_bytes && gnext - goff == align16((gbits + 7u) / 8u);
-    if (!group_ok) {
-      if (lane == 0) set_status(status, QLC_ERR_CORRUPT);
-      break;
-    }
-    // lane start bit (group-relative), ring fill, buffer fill
-    const uint32_t S = incl - bits;
-    d.gp = vbase + goff / 16;
-    d.vend = (uint32_t)((gnext - goff) / 16);
-    d.fv = S >> 7;
-    d.rpb = (S >> 5) * 4;
-    d.fetch();
-    cp_async_wait<0>();
-    d.hi = d.ring_word(d.rpb);
-    d.lo = d.ring_word(d.rpb + 4);
-    d.rpb += 8;
-    d.nxt = d.ring_word(d.rpb);
-    {
-      const uint32_t o = S & 31u;
-      d.hi = __funnelshift_l(d.lo, d.hi, o);
-      d.lo <<= o;
-      d.nb1 = 63u - o;
-    }
+  }
+  cp_async_wait<0>();
+  if (exists && d.p - S != bits) set_status(status, QLC_ERR_CORRUPT);
+}
 
-    // the two 16-symbol pieces of each block this lane writes out: piece q of
-    // rows r = lane / 2 and 16 + lane / 2 (their chunks' lengths and first
-    // symbol indices are fixed for the group)
-    const int q = lane & 1;
-    uint32_t row_n[2];
-    uint64_t row_i[2];
-#pragma unroll
-    for (int t = 0; t < 2; t++) {
-      const uint64_t rc = g * kGroupChunks + 16 * t + (lane >> 1);
-      row_n[t] = rc < h.n_chunks ? (uint32_t)min((uint64_t)cs, h.n - rc * cs) : 0u;
-      row_i[t] = rc * cs + 16 * q;
-    }
-    const uint32_t nmax = __reduce_max_sync(0xffffffffu, nsym);
-    for (uint32_t i0 = 0; i0 < nmax; i0 += kBlk) {
-      d.fetch3();
-      cp_async_wait<1>();
-      const uint32_t cnt = nsym > i0 ? min(kBlk, nsym - i0) : 0u;
-      if (cnt == kBlk) {
-#pragma unroll
-        for (int k = 0; k < (int)(kBlk / 16); k++) {
-          uint32_t w[4];
-#pragma unroll
-          for (int j = 0; j < 4; j++) {
-            const uint32_t p0 = d.round2(s_T, len_lo, len_hi);
-            const uint32_t p1 = d.round2(s_T, len_lo, len_hi);
-            w[j] = __byte_perm(p0, p1, 0x5410);
-          }
-          s_tile[lane * 2 + (k ^ ((lane >> 2) & 1))] = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-      } else if (cnt > 0) {
-        for (int k = 0; k < (int)(kBlk / 16); k++) {
-          uint32_t w[4];
-#pragma unroll
-          for (int j = 0; j < 4; j++) {
-            uint32_t v = 0;
-#pragma unroll
-            for (int q = 0; q < 4; q++)
-              if (16 * k + 4 * j + q < (int)cnt) v |= d.round1(s_T, len_lo, len_hi) << (8 * q);
-            w[j] = v;
-          }
-          s_tile[lane * 2 + (k ^ ((lane >> 2) & 1))] = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-      }
-      __syncwarp();
-      // the tile's row r is lane r's 32 output bytes: two 16-byte pieces per row
-      const bool ragged = __any_sync(0xffffffffu, i0 + kBlk > row_n[0] || i0 + kBlk > row_n[1]);
-      if (kOut == kOutCodes && !ragged) {
-        // every piece is whole: predicated streaming stores, no branch
-#pragma unroll
-        for (int t = 0; t < 2; t++) {
-          const int r = 16 * t + (lane >> 1);
-          const uint4 v = s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
-          put16_if(static_cast<uint8_t*>(out) + row_i[t] + i0, v, i0 + 16 * q < row_n[t]);
-        }
-      } else {
-#pragma unroll
-        for (int t = 0; t < 2; t++) {
-          const int r = 16 * t + (lane >> 1);
-          const uint32_t off = i0 + 16 * q;
-          if (off < row_n[t]) {
-            const uint4* src = &s_tile[r * 2 + (q ^ ((r >> 2) & 1))];
-            if (off + 16 <= row_n[t])
-              put16<kOut>(out, scales, row_i[t] + i0, *src);
-            else
-              put_tail<kOut>(out, scales, row_i[t] + i0, reinterpret_cast<const uint8_t*>(src), row_n[t] - off);
-          }
-        }
-      }
-      __syncwarp();
-    }
-    cp_async_wait<0>();
-    if (exists) {
-      // bits taken into the buffer minus bits still in it = bits consumed
-      const uint64_t consumed = (uint64_t)(d.rpb / 4 - (S >> 5)) * 32 - (d.nb1 + 1) - (S & 31u);
-      if (consumed != bits) set_status(status, QLC_ERR_CORRUPT);
-    }
-  } while (false);
+// Lane set-up shared by the kernels; 0 if the ring is not placed as its
+// addressing requires.
+__device__ __forceinline__ bool lane_init(DecShared& sm, LaneDec& d, int lane) {
+  d.lane4 = 4u * lane;
+  d.col_s = (uint32_t)__cvta_generic_to_shared(&sm.col[0][lane]);
+  d.stage_s = (uint32_t)__cvta_generic_to_shared(&sm.stage[0][lane]);
+  return (__cvta_generic_to_shared(sm.stage) & 15u) == 0;
 }
 
 // One container: every CTA (one warp) validates the header, builds its table
@@ -454,15 +449,15 @@ decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, void* __restric
   }
   if (blockIdx.x == 0 && lane == 0) *n_out = h.n;
   if (blockIdx.x >= h.n_groups) return;
-  if (__cvta_generic_to_shared(sm.ring) & 127u) {  // the ring addressing relies on it
+  LaneDec d;
+  if (!lane_init(sm, d, lane)) {
     if (lane == 0) set_status(status, QLC_ERR_CUDA);
     return;
   }
   build_table(in, sm, lane);
-  LaneDec d;
-  d.ring_s = (uint32_t)__cvta_generic_to_shared(&sm.ring[lane * kRingVec]);
+  const bool aligned32 = (reinterpret_cast<uintptr_t>(out) & 31u) == 0;
   for (uint64_t g = blockIdx.x; g < h.n_groups; g += gridDim.x)
-    decode_group<kOut>(h, in, out, scales, g, sm, d, status, lane);
+    decode_group<kOut>(h, in, out, scales, g, sm, d, status, lane, aligned32);
 }
 
 // A batch: warps take (shard, group) items from a device counter; a warp
@@ -473,13 +468,12 @@ decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
                     uint32_t* __restrict__ status) {
   __shared__ DecShared sm;
   const int lane = threadIdx.x;
-  if (__cvta_generic_to_shared(sm.ring) & 127u) {
+  LaneDec d;
+  if (!lane_init(sm, d, lane)) {
     if (lane == 0) set_status(status, QLC_ERR_CUDA);
     return;
   }
   const unsigned long long total = item_base[n_shards];
-  LaneDec d;
-  d.ring_s = (uint32_t)__cvta_generic_to_shared(&sm.ring[lane * kRingVec]);
   int cur = -1, bad = -1;
   DecHeader h;
   while (true) {
@@ -507,7 +501,8 @@ decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
       cur = sh;
     }
     if (g == 0 && lane == 0 && dd.out_bytes) *dd.out_bytes = h.n;
-    if (g < h.n_groups) decode_group<kOutCodes>(h, in, dd.out, nullptr, g, sm, d, status, lane);
+    const bool aligned32 = (reinterpret_cast<uintptr_t>(dd.out) & 31u) == 0;
+    if (g < h.n_groups) decode_group<kOutCodes>(h, in, dd.out, nullptr, g, sm, d, status, lane, aligned32);
   }
 }
 
