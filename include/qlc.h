@@ -63,7 +63,8 @@ typedef enum {
   QLC_ERR_CAPACITY = 2, /* an output or workspace buffer is too small */
   QLC_ERR_CORRUPT = 3,  /* container fails validation (device check) */
   QLC_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up */
-  QLC_ERR_CUDA = 5      /* a CUDA runtime call or launch failed */
+  QLC_ERR_CUDA = 5,     /* a CUDA runtime call or launch failed */
+  QLC_ERR_CHECK = 6     /* an index check failed (only the checked build checks) */
 } qlc_status;
 
 #define QLC_VERSION 1
@@ -175,10 +176,13 @@ qlc_status qlc_encode(const uint8_t *d_in, size_t n, const qlc_lut *d_lut,
  * most 65536 groups of 32 chunks (65536 * 32 * chunk_symbols symbols; e.g.
  * 8 GiB at chunk 4096); larger n returns QLC_ERR_CAPACITY.  The first call on
  * each device looks up that device's array address (with the device
- * current), so make the first call on a device before any stream capture.
- * All calls share the one array and each call clears it on `stream` before
- * use: calls that may run at the same time on the GPU (different streams
- * without ordering between them) race and must not be issued.  Other
+ * current), and so does the first call after the device's context changed
+ * (a device reset), so make those calls before any stream capture.  The
+ * address cache is safe to use from several host threads.  All calls share
+ * the one array and each call clears it on `stream` before use: calls that
+ * may run at the same time on the GPU (different streams without ordering
+ * between them, or calls from several host threads on one stream, whose
+ * clears and kernels may interleave) race and must not be issued.  Other
  * arguments, errors and alignment rules as for qlc_encode. */
 qlc_status qlc_encode_noalloc(const uint8_t *d_in, size_t n, const qlc_lut *d_lut,
                               uint32_t chunk_symbols, uint8_t *d_out, size_t out_cap,
@@ -191,7 +195,13 @@ qlc_status qlc_encode_noalloc(const uint8_t *d_in, size_t n, const qlc_lut *d_lu
  * is validated on the device (header fields, scheme, that dec is a
  * permutation, the group layout and that every chunk ends exactly at its
  * recorded bit count); a failure sets *d_status to QLC_ERR_CORRUPT and leaves
- * d_out partly written; out_cap < n sets QLC_ERR_CAPACITY.  Async on stream. */
+ * d_out partly written; out_cap < n sets QLC_ERR_CAPACITY.  Async on stream.
+ * Not every bit string is checked: the decoding rule is total, so a
+ * codeword of an area with 8 suffix bits whose suffix lies below that
+ * area's first rank (0..87 under Table 1, 0..97 under Table 2; no encoder
+ * writes one) decodes without error, as the rank equal to its suffix.  A
+ * corruption that only produces such codewords and keeps every chunk's bit
+ * count is therefore not detected. */
 qlc_status qlc_decode(const uint8_t *d_in, size_t in_bytes, uint8_t *d_out,
                       size_t out_cap, uint64_t *d_n_out, uint32_t *d_status,
                       qlc_stream_t stream);

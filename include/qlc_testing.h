@@ -25,6 +25,15 @@ qlc_status qlc_test_encode_stalled_lookback(const uint8_t *d_in, size_t n, const
                                             void *d_ws, size_t ws_bytes, uint64_t *d_out_bytes,
                                             uint32_t *d_status, qlc_stream_t stream);
 
+/* The checked build of the library (compiled with -DQLC_CHECKED) guards every
+ * index into global and shared memory that its kernels compute from data: an
+ * index out of its range skips the access, sets *d_status to QLC_ERR_CHECK
+ * where the call has a status word, and records where it happened.  This
+ * returns that record for the first failed check since the last call
+ * (file number << 16 | source line; 0 if no check failed) and clears it.
+ * Synchronises the device.  In a normal build it returns 0xFFFFFFFF. */
+uint32_t qlc_test_check_take(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@
 // 32 chunks) with a block-wide prefix sum; the persistent kernels then take
 // items from a device counter, so shards of very different sizes share the
 // GPU evenly and no host round trip is needed.
+#define QLC_FILE_ID 4
 #include "hist_cols.cuh"
 
 namespace qlc {
@@ -142,7 +143,7 @@ hist_batch_kernel(const qlc_desc* descs, int n_shards, const unsigned long long*
     while (s + 1 < n_shards && item_base[s + 1] <= t) s++;
     const int tgt = shared ? 0 : s;
     if (tgt != target) {
-      flush_cols(hc_sm, hists + (size_t)target * 256, tid);
+      flush_cols(hc_sm, hists + (size_t)(QLC_GUARD(target < n_shards, nullptr) ? target : 0) * 256, tid);
       target = tgt;
     }
     const unsigned long long e = min(t1, item_base[s + 1]);  // this CTA's items of shard s end here
@@ -151,8 +152,10 @@ hist_batch_kernel(const qlc_desc* descs, int n_shards, const unsigned long long*
     const uint64_t beg = (t - item_base[s]) * kHistItem;      // a multiple of 16
     const uint64_t end = min((uint64_t)((e - item_base[s]) * kHistItem), (uint64_t)d.in_bytes);
     const uint64_t vb = beg / 16, ve = end / 16;
-    count_span(reinterpret_cast<const uint4*>(in) + vb, ve - vb, col, tid);
-    count_bytes(in + ve * 16, end - ve * 16, col, tid);
+    if (QLC_GUARD(s < n_shards && beg <= end, nullptr)) {
+      count_span(reinterpret_cast<const uint4*>(in) + vb, ve - vb, col, tid);
+      count_bytes(in + ve * 16, end - ve * 16, col, tid);
+    }
     t = e;
   }
   flush_cols(hc_sm, hists + (size_t)target * 256, tid);
@@ -192,3 +195,7 @@ qlc_status qlc_histogram_batch(const qlc_desc* d_descs, int n_shards, uint64_t* 
 }
 
 }  // extern "C"
+
+namespace qlc {
+QLC_DEFINE_CHECK_TAKE(check_take_batch)
+}  // namespace qlc

@@ -22,6 +22,7 @@
 // streaming store.
 #include <cuda_bf16.h>
 
+#define QLC_FILE_ID 1
 #include "qlc_common.cuh"
 
 namespace qlc {
@@ -30,6 +31,7 @@ constexpr int kDecCtasPerSm = 20;  // 20 x (8.3 KB + 1 KB reserved); at 24 the r
 
 struct DecHeader {
   uint64_t n, payload_bytes, P, n_chunks, n_groups;
+  uint64_t in_bytes, out_cap;  // the caller's buffers (bounds of the checked build)
   uint32_t cs;
   uint32_t len_lo, len_hi;  // code length of areas 0-3 / 4-7, one byte each
 };
@@ -80,6 +82,8 @@ __device__ uint32_t parse_header(const uint8_t* in, uint64_t in_bytes, uint64_t 
   ok = ok && h->P <= in_bytes && h->payload_bytes <= in_bytes - h->P;
   if (!ok) return QLC_ERR_CORRUPT;
   if (out_cap < h->n) return QLC_ERR_CAPACITY;
+  h->in_bytes = in_bytes;
+  h->out_cap = out_cap;
   h->len_lo = h->len_hi = 0;
   for (int i = 0; i < 4; i++) {
     h->len_lo |= (3u + ab[i]) << (8 * i);
@@ -142,6 +146,7 @@ struct LaneDec {
   uint32_t tv;     // next vector to move from the staging ring to the column ring
   uint32_t fv;     // next vector to fetch
   uint32_t vend;   // vectors of this stream in the group
+  uint64_t vlim;   // vectors from the group's start to the end of the container (checked build)
   const uint4* gp; // the group's payload
   uint32_t lane4;      // byte offset of col[0][lane] in the column ring
   uint32_t col_s;      // shared address of col[0][lane]
@@ -153,7 +158,7 @@ struct LaneDec {
   __device__ __forceinline__ void fetch(uint32_t want) {
 #pragma unroll
     for (int i = 0; i < k; i++) {
-      const uint32_t q = fv < want;
+      const uint32_t q = fv < want && QLC_GUARD(fv < vlim, nullptr);
       asm volatile(
           "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q cp.async.cg.shared.global [%0], [%1], 16;\n\t}" ::"r"(
               stage_s + (fv % kStageVec) * 512),
@@ -243,10 +248,12 @@ struct LaneDec {
   __device__ __forceinline__ uint32_t round2(const DecShared& sm, uint32_t len_lo, uint32_t len_hi) {
     const uint32_t x = __funnelshift_l(lo, hi, p);
     const uint32_t la = code_len(x, len_lo, len_hi);
-    const uint32_t a = sm.T[__funnelshift_l(x, 0u, la)];
+    const uint32_t ia = __funnelshift_l(x, 0u, la);
+    const uint32_t a = QLC_GUARD(ia < 2048u, nullptr) ? sm.T[ia] : 0u;
     const uint32_t x2 = x << la;
     const uint32_t lb = code_len(x2, len_lo, len_hi);
-    const uint32_t b = sm.T[__funnelshift_l(x2, 0u, lb)];
+    const uint32_t ib = __funnelshift_l(x2, 0u, lb);
+    const uint32_t b = QLC_GUARD(ib < 2048u, nullptr) ? sm.T[ib] : 0u;
     step_to(sm, p + la + lb);
     return mad_lo(b, 256u, a);
   }
@@ -254,7 +261,8 @@ struct LaneDec {
   __device__ __forceinline__ uint32_t round1(const DecShared& sm, uint32_t len_lo, uint32_t len_hi) {
     const uint32_t x = __funnelshift_l(lo, hi, p);
     const uint32_t la = code_len(x, len_lo, len_hi);
-    const uint32_t a = sm.T[__funnelshift_l(x, 0u, la)];
+    const uint32_t ia = __funnelshift_l(x, 0u, la);
+    const uint32_t a = QLC_GUARD(ia < 2048u, nullptr) ? sm.T[ia] : 0u;
     step_to(sm, p + la);
     return a;
   }
@@ -269,7 +277,9 @@ __device__ void build_table(const uint8_t* in, DecShared& sm, int lane) {
   uint32_t base = 0;
   for (int i = 0; i < 8; i++) {
     const uint32_t b = in[40 + i];
-    for (uint32_t s = lane; s < (1u << b); s += 32) sm.T[(i << b) | s] = sm.dec[b == 8 ? s : base + s];
+    for (uint32_t s = lane; s < (1u << b); s += 32)
+      if (QLC_GUARD(((i << b) | s) < 2048u && (b == 8 ? s : base + s) < 256u, nullptr))
+        sm.T[(i << b) | s] = sm.dec[b == 8 ? s : base + s];
     base += *reinterpret_cast<const uint16_t*>(in + 24 + 2 * i);
   }
   __syncwarp();
@@ -377,7 +387,8 @@ __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* 
   const uint64_t c = g * kGroupChunks + lane;
   const bool exists = c < h.n_chunks;
   const uint32_t nsym = exists ? (uint32_t)min((uint64_t)cs, h.n - c * cs) : 0u;
-  const uint32_t bits = exists ? chunk_bits[c] : 0u;
+  const uint32_t bits =
+      exists && QLC_GUARD(kIndexOff + 8 * h.n_groups + 2 * (c + 1) <= h.in_bytes, status) ? chunk_bits[c] : 0u;
   uint32_t incl = bits;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -385,8 +396,10 @@ __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* 
     if (lane >= o) incl += t;
   }
   const uint32_t gbits = __shfl_sync(0xffffffffu, incl, 31);
-  const uint64_t goff = group_off[g];
-  const uint64_t gnext = g + 1 < h.n_groups ? group_off[g + 1] : h.payload_bytes;
+  const uint64_t goff = QLC_GUARD(kIndexOff + 8 * (g + 1) <= h.in_bytes, status) ? group_off[g] : 0ull;
+  const uint64_t gnext = g + 1 < h.n_groups
+                             ? (QLC_GUARD(kIndexOff + 8 * (g + 2) <= h.in_bytes, status) ? group_off[g + 1] : 0ull)
+                             : h.payload_bytes;
   const bool group_ok = (g != 0 || goff == 0) && (goff & 15u) == 0 && goff <= gnext &&
                         gnext <= h.payload_bytes && gnext - goff == align16((gbits + 7u) / 8u);
   if (!group_ok) {
@@ -397,6 +410,7 @@ __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* 
   const uint32_t S = incl - bits;
   d.gp = vbase + goff / 16;
   d.vend = (uint32_t)((gnext - goff) / 16);
+  d.vlim = (h.in_bytes - h.P - goff) / 16;  // goff <= payload_bytes <= in_bytes - P (validated)
   d.start(sm, S);
   const uint64_t i_chunk = c * cs;  // the chunk's first symbol
   const uint32_t nmax = __reduce_max_sync(0xffffffffu, nsym);
@@ -411,9 +425,12 @@ __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* 
         const uint32_t p1 = d.round2(sm, len_lo, len_hi);
         w[j] = __byte_perm(p0, p1, 0x5410);
       }
-      put32<kOut>(out, scales, i_chunk + i0, w, aligned32);
+      if (QLC_GUARD(i_chunk + i0 + kBlk <= h.out_cap, status)) put32<kOut>(out, scales, i_chunk + i0, w, aligned32);
     } else {
-      for (uint32_t k = 0; k < cnt; k++) put1<kOut>(out, scales, i_chunk + i0 + k, d.round1(sm, len_lo, len_hi));
+      for (uint32_t k = 0; k < cnt; k++) {
+        const uint32_t sym = d.round1(sm, len_lo, len_hi);
+        if (QLC_GUARD(i_chunk + i0 + k < h.out_cap, status)) put1<kOut>(out, scales, i_chunk + i0 + k, sym);
+      }
     }
   }
   cp_async_wait<0>();
@@ -563,3 +580,7 @@ extern "C" qlc_status qlc_decode_batch(const qlc_desc* d_descs, int n_shards, vo
   decode_batch_kernel<<<sm_count() * per_sm, 32, 0, st>>>(d_descs, n_shards, w.item_base, w.ticket, d_status);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
+
+namespace qlc {
+QLC_DEFINE_CHECK_TAKE(check_take_decode)
+}  // namespace qlc

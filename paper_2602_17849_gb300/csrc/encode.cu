@@ -16,6 +16,13 @@
 //           16-byte streaming stores of every completed 16-byte block; blocks
 //           shared by neighbouring chunks are merged once per group.
 // HBM traffic is one read of the input and one write of the container.
+#include <cuda.h>
+
+#include <mutex>
+#include <unordered_map>
+#include <utility>
+
+#define QLC_FILE_ID 2
 #include "qlc_common.cuh"
 #include "../../include/qlc_testing.h"
 
@@ -183,6 +190,8 @@ struct EncArgs {
   unsigned int* ticket;
   unsigned long long* gstat;
   uint32_t* status;
+  uint64_t out_cap;    // one tensor: bytes at out (batches: each descriptor's)
+  uint64_t gstat_cap;  // look-back words at gstat
 };
 
 // Packing state of one warp within one chunk.  The warp appends 512
@@ -198,6 +207,7 @@ struct Packer {
   uint32_t seam_s;       // shared address of the chunk's seam slot [0]
   uint32_t seam_idx_s;   // and of its block index
   uint32_t seam_blk;     // block shared with the previous chunk, ~0u if none
+  uint32_t blk_lim;      // 16-byte blocks available at dst (checked build)
   uint32_t base_bit;     // group-relative bit of the step's first symbol
   uint32_t win;          // group-relative word held at stage word 4 (a multiple of 4)
   uint32_t cur;          // staging buffer in use
@@ -206,6 +216,7 @@ struct Packer {
   // Moves block b (< nblk) of the current buffer out and zeroes it; branch-free.
   __device__ __forceinline__ void put_block(uint32_t b, uint32_t nblk, const uint32_t* sb) const {
     const uint32_t blk = win / 4 + b;
+    if (!QLC_GUARD(b >= nblk || blk < blk_lim, nullptr)) nblk = 0;
     const uint32_t sa = (uint32_t)__cvta_generic_to_shared(sb) + 16u * b;
     asm volatile(
         "{\n\t"
@@ -266,8 +277,8 @@ struct Packer {
     // first word also holds the previous lane's last bits, which that lane
     // ORs in afterwards with its partial last word.  Stores precede the ORs
     // in program order, and no two lanes store the same word.
-    {
-      const uint32_t p = base_bit + incl - L + 32u * (4u - win);  // bit relative to stage word 0
+    const uint32_t p = base_bit + incl - L + 32u * (4u - win);  // bit relative to stage word 0
+    if (QLC_GUARD(((p + L) >> 5) < (uint32_t)kWStage, nullptr)) {
       uint32_t wa = stage_s + cur * kWStage * 4 + (p >> 5) * 4;
       uint32_t nb = p & 31u;  // bits in hi
       uint32_t hi = ld_shared_u32(wa);
@@ -313,6 +324,7 @@ encode_kernel(EncArgs A) {
   __shared__ uint64_t s_n;
   __shared__ const qlc_lut* s_lut;
   __shared__ uint8_t* s_out;
+  __shared__ uint64_t s_cap;
   __shared__ unsigned long long* s_ob;
   __shared__ int s_err;
 
@@ -342,6 +354,7 @@ encode_kernel(EncArgs A) {
             s_n = d.in_bytes;
             s_lut = d.lut;
             s_out = static_cast<uint8_t*>(d.out);
+            s_cap = d.out_cap;
             s_ob = reinterpret_cast<unsigned long long*>(d.out_bytes);
           } else {
             s_first = 0;
@@ -349,6 +362,7 @@ encode_kernel(EncArgs A) {
             s_n = A.n;
             s_lut = A.lut;
             s_out = A.out;
+            s_cap = A.out_cap;
             s_ob = A.out_bytes;
           }
         }
@@ -424,7 +438,8 @@ encode_kernel(EncArgs A) {
         for (uint32_t t = nv * 16 + lane; t < m; t += 32) bits += enc_entry(tab, in[cbeg + t]);
         bits &= (1u << 21) - 1;  // a lane sums at most 4096 lengths of <= 11 bits
         bits = warp_sum_u32(bits);
-        if (lane == 0) chunk_bits[g * kGroupChunks + c] = (uint16_t)bits;
+        if (lane == 0 && QLC_GUARD(g * kGroupChunks + c < n_chunks, A.status))
+          chunk_bits[g * kGroupChunks + c] = (uint16_t)bits;
       }
       if (lane == 0) s_chunk_bits[c] = bits;
     }
@@ -444,15 +459,15 @@ encode_kernel(EncArgs A) {
       s_seam_idx[lane][0] = s_seam_idx[lane][1] = ~0u;
       const uint32_t gbits = __shfl_sync(0xffffffffu, incl, 31);
       const uint64_t gbytes = align16((gbits + 7) / 8);
-      bool err = false;
-      const unsigned long long excl = lookback(A.gstat, item, s_first, gbytes, lane, &err);
+      bool err = !QLC_GUARD(item < A.gstat_cap, A.status);
+      const unsigned long long excl = err ? 0ull : lookback(A.gstat, item, s_first, gbytes, lane, &err);
       if (lane == 0) {
         s_excl = excl;
         s_err = err;
         if (err) {
           set_status(A.status, QLC_ERR_TIMEOUT);
         } else {
-          group_off[g] = excl;
+          if (QLC_GUARD(g < n_groups, A.status)) group_off[g] = excl;
           if (g == n_groups - 1) {
             *reinterpret_cast<unsigned long long*>(out + 48) = excl + gbytes;
             if (s_ob) *s_ob = P + excl + gbytes;
@@ -472,12 +487,14 @@ encode_kernel(EncArgs A) {
       const uint64_t cbeg = gbeg + (uint64_t)c * cs;
       if (cbeg >= gend) break;
       const uint32_t m = (uint32_t)(min(cbeg + cs, gend) - cbeg);
+      if (!QLC_GUARD(cbeg + m <= n, A.status)) break;
       const uint32_t S = s_chunk_start[c];
       Packer pk;
       pk.tab = tab;
       pk.stage = &s_stage[warp][0][0];
       pk.stage_s = stage_s;
       pk.dst = dst;
+      pk.blk_lim = (uint32_t)min((uint64_t)((s_cap - P - s_excl) / 16), (uint64_t)0xFFFFFFFFu);
       pk.seam_s = (uint32_t)__cvta_generic_to_shared(&s_seam[c][0]);
       pk.seam_idx_s = (uint32_t)__cvta_generic_to_shared(&s_seam_idx[c][0]);
       pk.seam_blk = (S & 127u) ? (S >> 7) : ~0u;
@@ -541,7 +558,7 @@ encode_kernel(EncArgs A) {
             }
           }
         }
-        st_cs_v4(&dst[i1], v);
+        if (QLC_GUARD((uint64_t)i1 < (s_cap - P - s_excl) / 16, A.status)) st_cs_v4(&dst[i1], v);
       }
     }
   }
@@ -621,6 +638,8 @@ qlc_status qlc_encode(const uint8_t* d_in, size_t n, const qlc_lut* d_lut, uint3
   A.ticket = static_cast<unsigned int*>(d_ws);
   A.gstat = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(d_ws) + 16);
   A.status = d_status;
+  A.out_cap = out_cap;
+  A.gstat_cap = (ws_bytes - 16) / 8;
   encode_kernel<<<enc_grid(A.n_items, nullptr), kEncThreads, 0, st>>>(A);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
@@ -653,6 +672,8 @@ qlc_status qlc_test_encode_stalled_lookback(const uint8_t* d_in, size_t n, const
   A.ticket = static_cast<unsigned int*>(d_ws);
   A.gstat = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(d_ws) + 16);
   A.status = d_status;
+  A.out_cap = out_cap;
+  A.gstat_cap = (ws_bytes - 16) / 8;
   encode_kernel<<<enc_grid(A.n_items, nullptr), kEncThreads, 0, st>>>(A);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
@@ -676,6 +697,7 @@ qlc_status qlc_encode_batch(const qlc_desc* d_descs, int n_shards, uint32_t chun
   A.ticket = w.ticket;
   A.gstat = w.gstat;
   A.status = d_status;
+  A.gstat_cap = w.gstat_cap;
   // the item count is only known on the device: launch the full resident grid
   encode_kernel<<<enc_grid(~0ull, h_launch), kEncThreads, 0, st>>>(A);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
@@ -698,24 +720,59 @@ constexpr uint64_t kNoAllocMaxGroups = 65536;
 constexpr size_t kNoAllocScratchBytes = 16 + 8 * kNoAllocMaxGroups;  // 512 KiB + 16 B
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device with that
-// device current (the host-side symbol is not a device address).
+// Unique id of the calling thread's current CUDA context, 0 if there is none
+// or the driver cannot report it.  The driver entry points come through the
+// runtime, so the library needs no link to the driver library.
+static unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of g_noalloc_scratch in the current device's context (the
+// host-side symbol is not a device address).  It is looked up with the
+// device current on the first call, and again whenever the device's context
+// has changed since (a reset destroys the old context, and the array moves
+// with the new one); without a context id from the driver it is looked up
+// on every call.  The cache is shared by all host threads and guarded by a
+// mutex.
 static void* noalloc_scratch_ptr(qlc_status* err) {
-  static void* cached[64] = {nullptr};
+  static std::mutex mu;
+  static std::unordered_map<int, std::pair<unsigned long long, void*>> cache;  // device -> (context id, address)
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  if (cudaGetDevice(&dev) != cudaSuccess) {
     *err = QLC_ERR_CUDA;
     return nullptr;
   }
-  if (!cached[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      *err = QLC_ERR_CUDA;
-      return nullptr;
-    }
-    cached[dev] = p;
+  const unsigned long long id = current_context_id();
+  std::lock_guard<std::mutex> lock(mu);
+  const auto it = cache.find(dev);
+  if (it != cache.end() && id != 0 && it->second.first == id) return it->second.second;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    *err = QLC_ERR_CUDA;
+    return nullptr;
   }
-  return cached[dev];
+  // the lookup makes the device's primary context current if none was
+  cache[dev] = {current_context_id(), p};
+  return p;
 }
 }  // namespace qlc
 
@@ -734,3 +791,7 @@ extern "C" qlc_status qlc_encode_noalloc(const uint8_t* d_in, size_t n, const ql
   return qlc_encode(d_in, n, d_lut, chunk_symbols, d_out, out_cap, ws, kNoAllocScratchBytes,
                     d_out_bytes, d_status, stream);
 }
+
+namespace qlc {
+QLC_DEFINE_CHECK_TAKE(check_take_encode)
+}  // namespace qlc

@@ -42,7 +42,10 @@ __device__ __forceinline__ void prefetch_batch(const uint4* v, uint64_t i, uint6
 // col: shared address of this lane's column (value 0); value b is b * 128 bytes on.
 __device__ __forceinline__ void count_word(uint32_t col, uint32_t w) {
 #pragma unroll
-  for (int j = 0; j < 4; j++) red_add_one(col + (__byte_perm(w, 0, 0x4440 + j) << 7));
+  for (int j = 0; j < 4; j++) {
+    const uint32_t b = __byte_perm(w, 0, 0x4440 + j);
+    if (QLC_GUARD(b < 256u, nullptr)) red_add_one(col + (b << 7));
+  }
 }
 __device__ __forceinline__ void count_vec(uint32_t col, uint4 q) {
   count_word(col, q.x);
@@ -90,6 +93,7 @@ __device__ __forceinline__ void count_span(const uint4* __restrict__ v, uint64_t
     }
   }
   for (; i < nvec; i += T) count_vec(col, ldg_nc_v4(v + i));
+  QLC_GUARD(i >= nvec && i - nvec < T, nullptr);  // the loop ended at the span's end
 }
 
 // Counts m single bytes at p (a ragged end), CTA-strided.

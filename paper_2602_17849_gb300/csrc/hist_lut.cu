@@ -1,8 +1,11 @@
 // hist_lut.cu -- byte histogram (Section 4) and LUT construction (Section 7)
 // kernels of libqlc, plus their C-ABI entry points.
+#define QLC_FILE_ID 3
 #include "hist_cols.cuh"
+#include "../../include/qlc_testing.h"
 
 #include <algorithm>
+#include <atomic>
 #include <functional>
 
 namespace qlc {
@@ -125,13 +128,18 @@ lut_best_kernel(const unsigned long long* __restrict__ hists, SchemeSet set, qlc
 }
 
 int sm_count() {
-  static int cached[64] = {0};
+  // one atomic slot per device below 64 (any thread may fill it; all write
+  // the same value); other devices ask the runtime each time
+  static std::atomic<int> cached[64];
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 148;
-  if (dev < 64 && cached[dev]) return cached[dev];
+  if (dev < 64) {
+    const int c = cached[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
   int v = 0;
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-  if (dev < 64) cached[dev] = v;
+  if (dev < 64) cached[dev].store(v, std::memory_order_relaxed);
   return v;
 }
 
@@ -172,6 +180,7 @@ const char* qlc_status_string(qlc_status s) {
     case QLC_ERR_CORRUPT: return "corrupt container";
     case QLC_ERR_TIMEOUT: return "device wait timed out";
     case QLC_ERR_CUDA: return "CUDA error";
+    case QLC_ERR_CHECK: return "index check failed";
   }
   return "unknown status";
 }
@@ -348,3 +357,19 @@ qlc_status qlc_peek_header(const void* h_hdr, size_t hdr_bytes, uint64_t* n, uin
 }
 
 }  // extern "C"
+
+namespace qlc {
+QLC_DEFINE_CHECK_TAKE(check_take_hist)
+}  // namespace qlc
+
+extern "C" uint32_t qlc_test_check_take(void) {
+#ifdef QLC_CHECKED
+  const uint32_t v[5] = {qlc::check_take_decode(), qlc::check_take_encode(), qlc::check_take_hist(),
+                         qlc::check_take_batch(), qlc::check_take_quant()};
+  for (uint32_t x : v)
+    if (x) return x;
+  return 0;
+#else
+  return 0xFFFFFFFFu;
+#endif
+}

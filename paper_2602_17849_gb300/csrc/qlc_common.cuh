@@ -54,6 +54,53 @@ __device__ __forceinline__ void set_status(uint32_t* st, uint32_t code) {
   if (st) atomicCAS(st, 0u, code);
 }
 
+// Checked build (-DQLC_CHECKED): QLC_GUARD(cond, status) is false when an
+// index check fails; the caller then skips the access.  The first failure of
+// each .cu file is recorded in that file's g_check_site (file number << 16 |
+// line) and, where a status word is at hand, as QLC_ERR_CHECK.  In a normal
+// build the guard is the constant true and compiles away.
+#ifndef QLC_FILE_ID
+#define QLC_FILE_ID 0
+#endif
+#ifdef QLC_CHECKED
+static __device__ uint32_t g_check_site = 0;
+#endif
+__device__ __forceinline__ bool guard(bool ok, uint32_t* status, uint32_t site) {
+#ifdef QLC_CHECKED
+  if (!ok) {
+    atomicCAS(&g_check_site, 0u, site);
+    set_status(status, QLC_ERR_CHECK);
+  }
+  return ok;
+#else
+  (void)status;
+  (void)site;
+  return true;
+#endif
+}
+#define QLC_GUARD(cond, status) (::qlc::guard((cond), (status), ((uint32_t)QLC_FILE_ID << 16) | __LINE__))
+
+// Host side of the checked build: reads and clears this file's record.
+// Each .cu file defines its own with QLC_DEFINE_CHECK_TAKE(name).
+#ifdef QLC_CHECKED
+#define QLC_DEFINE_CHECK_TAKE(name)                                       \
+  uint32_t name() {                                                       \
+    uint32_t v = 0, z = 0;                                                \
+    if (cudaDeviceSynchronize() != cudaSuccess) return 0xFFFFFFFEu;       \
+    if (cudaMemcpyFromSymbol(&v, g_check_site, 4) != cudaSuccess) return 0xFFFFFFFEu; \
+    cudaMemcpyToSymbol(g_check_site, &z, 4);                              \
+    return v;                                                             \
+  }
+#else
+#define QLC_DEFINE_CHECK_TAKE(name) \
+  uint32_t name() { return 0; }
+#endif
+uint32_t check_take_decode();
+uint32_t check_take_encode();
+uint32_t check_take_hist();
+uint32_t check_take_batch();
+uint32_t check_take_quant();
+
 // Big-endian view of a little-endian 32-bit word: byte 0 becomes bits 31..24,
 // so the first bit of the stream is the word's most significant bit.
 __device__ __forceinline__ uint32_t bswap32(uint32_t w) { return __byte_perm(w, 0, 0x0123); }

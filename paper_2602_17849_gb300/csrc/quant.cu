@@ -15,6 +15,7 @@
 // step butterfly.  Codes leave as one 4- (or 8-) byte store per lane.
 #include <cuda_bf16.h>
 
+#define QLC_FILE_ID 5
 #include "qlc_common.cuh"
 
 namespace qlc {
@@ -157,7 +158,7 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
 #pragma unroll
         for (int j = 0; j < E; j++) c[j] = e4m3_rne(v[u][j] / scale);
       }
-      if (i < n && (lane % kLanesPerBlock) == 0) scales[i / 32] = scale;
+      if (i < n && (lane % kLanesPerBlock) == 0 && QLC_GUARD(i / 32 < (n + 31) / 32, status)) scales[i / 32] = scale;
       if (i + E <= n) {
         if (E == 4) {
           *reinterpret_cast<uint32_t*>(codes + i) = c[0] | c[1] << 8 | c[2] << 16 | c[3] << 24;
@@ -167,13 +168,14 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
         }
         if (hist) {
 #pragma unroll
-          for (int j = 0; j < E; j++) atomicAdd(&my[c[j] + (c[j] >> 7)], 1u);
+          for (int j = 0; j < E; j++)
+            if (QLC_GUARD(c[j] < 256u, status)) atomicAdd(&my[c[j] + (c[j] >> 7)], 1u);
         }
       } else {
         for (int j = 0; j < E; j++) {
           if (i + j < n) {
             codes[i + j] = (uint8_t)c[j];
-            if (hist) atomicAdd(&my[c[j] + (c[j] >> 7)], 1u);
+            if (hist && QLC_GUARD(c[j] < 256u, status)) atomicAdd(&my[c[j] + (c[j] >> 7)], 1u);
           }
         }
       }
@@ -289,3 +291,7 @@ extern "C" qlc_status qlc_dequantize_e4m3(const uint8_t* d_codes, const float* d
     dequantize_kernel<QLC_DTYPE_BF16><<<grid, 256, 0, st>>>(d_codes, d_scales, n, d_out);
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
+
+namespace qlc {
+QLC_DEFINE_CHECK_TAKE(check_take_quant)
+}  // namespace qlc

@@ -14,7 +14,7 @@ import torch
 
 from . import _build
 
-OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA = range(6)
+OK, ERR_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_TIMEOUT, ERR_CUDA, ERR_CHECK = range(7)
 CHUNKS_PER_GROUP = 32
 HEADER_BYTES = 64
 INDEX_OFFSET = 320
@@ -52,9 +52,10 @@ assert ctypes.sizeof(qlc_desc) == 48 and ctypes.sizeof(qlc_launch) == 8
 
 
 def _load() -> ctypes.CDLL:
-    path = _build.LIB
+    # QLC_LIBRARY names another build of the same library (the tests' checked build)
+    path = os.environ.get("QLC_LIBRARY", _build.LIB)
     if not os.path.exists(path):
-        raise ImportError(f"libqlc.so is not built ({path}); run __graft_entry__.build()")
+        raise ImportError(f"libqlc is not built ({path}); run __graft_entry__.build()")
     L = ctypes.CDLL(path)
     P, sz, u32, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_int
     L.qlc_version.restype = i32

@@ -27,30 +27,49 @@ def _lib():
     return qlc, L
 
 
+def _same_as_encode(qlc, L, x, cs):
+    """Encodes x with qlc_encode (caller workspace) and with qlc_encode_noalloc
+    and checks that the containers are identical."""
+    n = x.numel()
+    stream = torch.cuda.current_stream()
+    codec = qlc.Codec(n, cs, 1)
+    ref = codec.new_container()
+    codec.encode_into(x, ref)                   # histogram, LUT, qlc_encode
+    torch.cuda.synchronize()
+    codec.check()
+    ref_bytes = int(codec.out_bytes.item())
+
+    out = torch.full((codec.cap,), 0x5A, dtype=torch.uint8, device="cuda")
+    nb = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = L.qlc_encode_noalloc(x.data_ptr(), n, codec.lut.data_ptr(), cs, out.data_ptr(),
+                              codec.cap, nb.data_ptr(), st.data_ptr(), stream.cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert int(nb.item()) == ref_bytes
+    assert torch.equal(out[:ref_bytes], ref[:ref_bytes])
+
+
 def test_noalloc_encode_equals_encode_on_two_calls():
     assert torch.cuda.is_available()
     qlc, L = _lib()
     from paper_2602_17849_gb300 import inputs
-    stream = torch.cuda.current_stream()
     for seed, n, cs in [(1, 3 * 32 * 4096 + 12345, 4096), (2, 1 << 20, 1024)]:
-        x = inputs.make_e4m3("t4", n, seed=seed).cuda()
-        codec = qlc.Codec(n, cs, 1)
-        ref = codec.new_container()
-        codec.encode_into(x, ref)                   # histogram, LUT, qlc_encode
-        torch.cuda.synchronize()
-        codec.check()
-        ref_bytes = int(codec.out_bytes.item())
+        _same_as_encode(qlc, L, inputs.make_e4m3("t4", n, seed=seed).cuda(), cs)
 
-        out = torch.full((codec.cap,), 0x5A, dtype=torch.uint8, device="cuda")
-        nb = torch.zeros(1, dtype=torch.int64, device="cuda")
-        st = torch.zeros(1, dtype=torch.int32, device="cuda")
-        rc = L.qlc_encode_noalloc(x.data_ptr(), n, codec.lut.data_ptr(), cs, out.data_ptr(),
-                                  codec.cap, nb.data_ptr(), st.data_ptr(), stream.cuda_stream)
-        assert rc == 0
-        torch.cuda.synchronize()
-        assert int(st.item()) == 0
-        assert int(nb.item()) == ref_bytes
-        assert torch.equal(out[:ref_bytes], ref[:ref_bytes])
+
+def test_noalloc_accepts_exactly_the_limit():
+    """65536 groups of 32 chunks is the largest input the built-in array
+    holds; at chunk 128 that is 256 MiB, and the container still equals
+    qlc_encode's."""
+    qlc, L = _lib()
+    from paper_2602_17849_gb300 import inputs
+    cs = 128
+    x = inputs.make_e4m3("t4", 65536 * 32 * cs, seed=7, device="cuda")
+    _same_as_encode(qlc, L, x, cs)
+    del x
+    torch.cuda.empty_cache()
 
 
 def test_noalloc_rejects_too_many_groups():
