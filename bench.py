@@ -442,6 +442,33 @@ def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152,
                            out_cap=x.numel(), stream=stream)
 
     plain_ms = timed(plain_round_trip, 3)
+
+    # the same per-tensor launches spread round-robin over four streams (as
+    # the server runs its batches), each shard's encode and decode on one
+    # stream: the concurrent baseline
+    pool = [torch.cuda.Stream(device=dev) for _ in range(4)]
+
+    def plain_multistream():
+        start = torch.cuda.Event()
+        start.record(stream)
+        for s in pool:
+            s.wait_event(start)
+        for i, x in enumerate(shards):
+            s = pool[i % 4]
+            qlc.qlc_histogram(x, hist[i], stream=s)
+            qlc.qlc_build_lut(hist[i], SCHEME, luts[i], stream=s)
+            qlc.qlc_encode(x, luts[i], cs, b.container(i), ws[ws_off[i]:ws_off[i + 1]], cbytes[i:i + 1],
+                           b.status, stream=s)
+            qlc.qlc_decode(b.container(i), b.output(i), nout[i:i + 1], b.status, in_bytes=caps[i],
+                           out_cap=x.numel(), stream=s)
+        for s in pool:
+            done = torch.cuda.Event()
+            done.record(s)
+            stream.wait_event(done)
+
+    plain_ms_4s = timed(plain_multistream, 3)
+    b.check()
+    exact = exact and all(torch.equal(b.output(i), x) for i, x in enumerate(shards))
     g = torch.cuda.CUDAGraph()
     s2 = torch.cuda.Stream(device=dev)
     s2.wait_stream(stream)
@@ -473,8 +500,10 @@ def batched_leg(dev, steps: int, warmup: int, peak: float, n_shards: int = 1152,
         "encode_roofline_frac": enc_bytes / (enc_ms * 1e-3) / 1e9 / peak,
         "encode_bytes_counted": "(2 + r) N: histogram read + encode read + container write",
         "plain_per_tensor_eager_ms": plain_ms, "plain_per_tensor_graph_ms": plain_graph_ms,
+        "plain_per_tensor_4streams_ms": plain_ms_4s,
         "batched_ms": rt_ms, "speedup_vs_plain_eager": plain_ms / rt_ms,
-        "speedup_vs_plain_graph": plain_graph_ms / rt_ms, "bit_exact_round_trip": bool(exact),
+        "speedup_vs_plain_graph": plain_graph_ms / rt_ms, "speedup_vs_plain_4streams": plain_ms_4s / rt_ms,
+        "bit_exact_round_trip": bool(exact),
         "launches_per_round_trip": {"batched": 7, "plain": 4 * n},
     }
 
@@ -561,12 +590,45 @@ def serve_leg(dev, seconds: float):
     wl = serve.CudaWorkload(dev, data_bytes=1 << 30, n_containers=128, min_size=4 << 10,
                             max_size=64 << 20, seed=3000)
     torch.cuda.empty_cache()
+    # A sample of the results (every 499th request of at most 16 MiB, up to
+    # 24) is copied aside on the device as it completes, without a host wait
+    # in the serving loop, and checked afterwards: a container must decode
+    # (with the library) to its request's input, decoded bytes must equal the
+    # source the container was made from.  The oracle comparison of served
+    # results at this scale is a GPU test.
+    qlc_cap = 17 << 20
+    keep = torch.empty(24 * qlc_cap, dtype=torch.uint8, device=dev)
+    side = torch.cuda.Stream(device=dev)
+    kept = []
+
+    def sample(r, ex):
+        if r.rid % 499 or len(kept) >= 24 or r.status != 0:
+            return
+        off, nb = r.result
+        if nb > qlc_cap or (r.n_in if r.kind == "compress" else r.n_out) > 16 << 20:
+            return
+        slot = len(kept) * qlc_cap
+        with torch.cuda.stream(side):
+            keep[slot:slot + nb].copy_(ex.dev_arena[off:off + nb], non_blocking=True)
+        kept.append((r, slot, nb))
+
     reqs, ex, srv, wall = serve.serve_run(dev, rate_hz=20_000, duration_s=seconds, budget_bytes=8 << 30,
-                                          workload=wl, seed=3001)
+                                          workload=wl, seed=3001, on_complete=sample)
     done = [r for r in reqs if r.done is not None]
     lat = serve.percentiles([r.latency for r in done])
     raw = sum(r.n_in if r.kind == "compress" else r.n_out for r in done)
     ok = all(r.status == 0 for r in done)
+    torch.cuda.synchronize()
+    from paper_2602_17849_gb300 import qlc
+    exact = True
+    for r, slot, nb in kept:
+        got = keep[slot:slot + nb]
+        if r.kind == "compress":
+            exact = exact and torch.equal(qlc.decode(got), wl.pool[r.in_ref:r.in_ref + r.n_in])
+        else:
+            _off, _nb, n, src_off = next(c for c in wl.containers if c[0] == r.in_ref)
+            exact = exact and torch.equal(got, wl.pool[src_off:src_off + n])
+    del keep
     return {
         "workload": "Poisson 20k req/s, 50/50 compress/decompress, 4 KiB-64 MiB log-uniform t4 e4m3, "
                     "8 GiB budget, 4 streams",
@@ -574,6 +636,10 @@ def serve_leg(dev, seconds: float):
         "p50_ms": lat[50] * 1e3 if lat[50] is not None else None,
         "p99_ms": lat[99] * 1e3 if lat[99] is not None else None,
         "raw_gbs": raw / wall / 1e9, "offered_gbs": raw / seconds / 1e9, "wall_s": wall, "all_status_ok": ok,
+        "checked_requests": len(kept),
+        "checked": "every 499th completed request of at most 16 MiB (up to 24), copied aside on the device "
+                   "as it completed; containers decoded back to their input, decoded bytes against the source",
+        "round_trip_exact": bool(exact) if kept else None,
     }
 
 

@@ -50,3 +50,48 @@ def test_serving_mix_equals_alone_and_oracle():
         s1.drain()
         assert alone.status == 0
         assert np.array_equal(got[r.rid], mixed[r.rid]), r.rid
+
+
+def test_serving_at_full_scale_sample_matches_oracle():
+    """The serving workload at full scale (Poisson 20,000 requests/s, sizes
+    log-uniform 4 KiB - 64 MiB, 8 GiB budget, 4 streams) for two seconds; a
+    sample of the completed requests (every 331st, up to 12, any size) is
+    copied aside on the device as it completes and compared byte for byte
+    with the oracle's container (compress) or the source bytes (decompress)."""
+    from paper_2602_17849_gb300 import _build
+    _build.build()
+    from paper_2602_17849_gb300 import serve
+    dev = torch.device("cuda")
+    wl = serve.CudaWorkload(dev, data_bytes=1 << 30, n_containers=32, min_size=4 << 10,
+                            max_size=64 << 20, seed=3000)
+    slot_bytes = (64 << 20) + (24 << 20)          # a 64 MiB input's worst-case container fits
+    keep = torch.empty(12 * slot_bytes, dtype=torch.uint8, device=dev)
+    side = torch.cuda.Stream(device=dev)
+    kept = []
+
+    def sample(r, ex):
+        if r.rid % 331 or len(kept) >= 12 or r.status != 0:
+            return
+        off, nb = r.result
+        slot = len(kept) * slot_bytes
+        with torch.cuda.stream(side):
+            keep[slot:slot + nb].copy_(ex.dev_arena[off:off + nb], non_blocking=True)
+        kept.append((r, slot, nb))
+
+    reqs, ex, srv, wall = serve.serve_run(dev, rate_hz=20_000, duration_s=2.0, budget_bytes=8 << 30,
+                                          workload=wl, seed=3001, on_complete=sample)
+    torch.cuda.synchronize()
+    assert len(reqs) > 30_000
+    assert all(r.done is not None and r.status == 0 for r in reqs)
+    assert len(kept) == 12
+    kinds = {r.kind for r, _, _ in kept}
+    assert kinds == {"compress", "decompress"}
+    for r, slot, nb in kept:
+        got = keep[slot:slot + nb].cpu().numpy()
+        if r.kind == "compress":
+            src = wl.pool[r.in_ref:r.in_ref + r.n_in].cpu().numpy()
+            want = oracle.encode(src, scheme_id=1, chunk_symbols=4096)
+        else:
+            _off, _nb, n, src_off = next(c for c in wl.containers if c[0] == r.in_ref)
+            want = wl.pool[src_off:src_off + n].cpu().numpy()
+        assert np.array_equal(got, want), (r.rid, r.kind, r.n_in)
