@@ -362,8 +362,26 @@ __device__ __forceinline__ void put32(void* out, const float* scales, uint64_t i
   if (kOut == kOutCodes) {
     st_cs_32(static_cast<uint8_t*>(out) + i, w, aligned32);
   } else {
-    put16<kOut>(out, scales, i, make_uint4(w[0], w[1], w[2], w[3]));
-    put16<kOut>(out, scales, i + 16, make_uint4(w[4], w[5], w[6], w[7]));
+    // the block's 32 values share one scale (i is a multiple of 32); they go
+    // out in whole 32-byte sectors: 4 stores of 8 fp32, or 2 of 16 bf16
+    const float sc = scales[i / 32];
+    uint32_t v[kOut == QLC_DTYPE_F32 ? 32 : 16];
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+      const float y = e4m3_to_f32((w[j >> 2] >> (8 * (j & 3))) & 0xFFu) * sc;
+      if (kOut == QLC_DTYPE_F32) {
+        v[j] = __float_as_uint(y);
+      } else if (j & 1) {
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(__uint_as_float(v[j >> 1]), y);
+        v[j >> 1] = *reinterpret_cast<const uint32_t*>(&hb);
+      } else {
+        v[j >> 1] = __float_as_uint(y);
+      }
+    }
+    constexpr int kVec = kOut == QLC_DTYPE_F32 ? 4 : 2;  // 32-byte pieces
+    uint8_t* dst = static_cast<uint8_t*>(out) + i * (kOut == QLC_DTYPE_F32 ? 4 : 2);
+#pragma unroll
+    for (int k = 0; k < kVec; k++) st_cs_32(dst + 32 * k, v + 8 * k, aligned32);
   }
 }
 
