@@ -15,6 +15,8 @@
 // step butterfly.  Codes leave as one 4- (or 8-) byte store per lane.
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #define QLC_FILE_ID 5
 #include "qlc_common.cuh"
 
@@ -22,7 +24,8 @@ namespace qlc {
 
 constexpr int kQuantWarps = 8;
 constexpr int kQuantThreads = kQuantWarps * 32;
-constexpr int kQuantUnroll = 2;
+constexpr int kQuantDepth = 4;  // input ring slots per thread
+constexpr int kQuantVec = 2;    // 16-byte input vectors per lane and step
 
 // The e4m3 byte nearest to v, ties to the even code, saturating (|v| finite).
 // With k = max(exponent of |v|, -6), the grid of e4m3 values around |v| is
@@ -38,25 +41,45 @@ __device__ __forceinline__ uint32_t e4m3_rne(float v) {
   return min(code, 0x7Fu) | ((u >> 24) & 0x80u);
 }
 
-// The same rounding of q0 = x * (1 / scale), which is not the quotient the
-// rule names (x / scale, rounded once) but lies within 2^-23 |x / scale| of
-// it: both 1 / scale and the product are rounded to nearest.  The code is a
-// step function of the value whose steps sit at the midpoints between
-// neighbouring e4m3 magnitudes, exact fp32 numbers, so q0 and the rounded
-// quotient get the same code unless one of them lies within 2^-22 |q0| of a
-// midpoint.  In grid units (t = |q0| 2^(3-k), |q0| < 2^(k+1)) that margin is
-// under 2^-18 of a step; *near is set when t lies within 2^-17 of a midpoint,
-// and the caller then takes the exact division.  Outside the margin the code
-// is the rule's, so the result is exact either way.
-__device__ __forceinline__ uint32_t e4m3_rne_or_near(float q0, bool* near) {
-  const uint32_t u = __float_as_uint(q0);
-  const int e = (int)((u >> 23) & 0xFFu) - 127;
-  const int k = max(e, -6);
-  const float t = fabsf(q0) * __uint_as_float((uint32_t)(130 - k) << 23);
-  const float rt = rintf(t);
-  *near = fabsf(t - rt) > 0.5f - 0x1p-17f;  // t - rt is exact
-  const uint32_t code = (uint32_t)(8 * k + 48) + (uint32_t)rt;
-  return min(code, 0x7Fu) | ((u >> 24) & 0x80u);
+// Codes of two products q = x * y, y within 2 ulp of 1 / scale, from the
+// hardware conversion to e4m3 (round to nearest even).  Below 448 its grid is
+// this format's grid (subnormals m 2^-9, normals (1 + m/8) 2^(e-7), sign bit
+// 7), so the codes agree there; it saturates at 448 (0x7E), and this format
+// goes on to 480 (0x7F), the code of every magnitude above the midpoint 464.
+// The rule rounds the quotient x / scale once; q is within 2^-21.6 |q| of it
+// (y's error and the product's rounding).  Each value is converted twice,
+// moved up and down by 2^-20 of itself, which brackets the quotient: both
+// codes equal (the code is monotone in the value) means the quotient has
+// that code too.  Above 464 the code's low bit is set by a flag computed on
+// the FMA pipe: (|v| - 464) 2^20 clamped to [0, 1] is 1.0 above 464 (the
+// fp32 neighbours of 464 are 2^-15 away) and 0.0 up to it, and
+// f0 + 256 f1 + 2^23 holds the two flags in its low bits, one per byte.
+// Returns the upper side's codes (qa | qb << 8); the two sides' differences,
+// flags included, are ORed into *diff: nonzero means the caller takes the
+// exact division.
+__device__ __forceinline__ uint32_t sat_flags(float a, float b) {
+  const float fa = __saturatef(fmaf(fabsf(a), 0x1p20f, -464.0f * 0x1p20f));
+  const float fb = __saturatef(fmaf(fabsf(b), 0x1p20f, -464.0f * 0x1p20f));
+  return __float_as_uint(fmaf(fb, 256.0f, fa + 0x1p23f));
+}
+__device__ __forceinline__ uint32_t e4m3x2_bracket(float qa, float qb, uint32_t* diff) {
+  constexpr float d = 0x1p-20f;
+  const float ua = fmaf(qa, d, qa), ub = fmaf(qb, d, qb);  // the larger magnitudes
+  const float la = fmaf(qa, -d, qa), lb = fmaf(qb, -d, qb);
+  uint16_t cu, cl;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(cu) : "f"(ub), "f"(ua));
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(cl) : "f"(lb), "f"(la));
+  const uint32_t up = (uint32_t)cu | (sat_flags(ua, ub) & 0x0101u);  // 0x7E -> 0x7F above 464
+  const uint32_t lo = (uint32_t)cl | (sat_flags(la, lb) & 0x0101u);
+  *diff |= up ^ lo;
+  return up;
+}
+
+// max(a, b) that returns NaN when either is NaN.
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
 }
 
 template <int kDtype>
@@ -64,123 +87,174 @@ struct QuantIo;
 
 template <>
 struct QuantIo<QLC_DTYPE_F32> {
-  static constexpr int kPerLane = 4;
-  __device__ static void load(const void* x, uint64_t i, uint64_t n, float* v) {
-    const float* p = static_cast<const float*>(x) + i;
-    if (i + 4 <= n) {
-      const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-      v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
-    } else {
-      for (int j = 0; j < 4; j++) v[j] = i + j < n ? p[j] : 0.0f;
-    }
+  static constexpr int kPerVec = 4;
+  __device__ static void unpack(uint4 q, float* v) {
+    v[0] = __uint_as_float(q.x), v[1] = __uint_as_float(q.y), v[2] = __uint_as_float(q.z),
+    v[3] = __uint_as_float(q.w);
+  }
+  __device__ static void load_tail(const void* x, uint64_t i, uint64_t n, float* v) {
+    const float* p = static_cast<const float*>(x);
+    for (int j = 0; j < 4 * kQuantVec; j++) v[j] = i + j < n ? p[i + j] : 0.0f;
   }
 };
 
 template <>
 struct QuantIo<QLC_DTYPE_BF16> {
-  static constexpr int kPerLane = 8;
-  __device__ static void load(const void* x, uint64_t i, uint64_t n, float* v) {
-    const uint16_t* p = static_cast<const uint16_t*>(x) + i;
-    if (i + 8 <= n) {
-      const uint4 q = ldg_nc_v4(reinterpret_cast<const uint4*>(p));
-      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+  static constexpr int kPerVec = 8;
+  __device__ static void unpack(uint4 q, float* v) {
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int j = 0; j < 4; j++) {
-        v[2 * j] = __uint_as_float(w[j] << 16);
-        v[2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
-      }
-    } else {
-      for (int j = 0; j < 8; j++) v[j] = i + j < n ? __uint_as_float((uint32_t)p[j] << 16) : 0.0f;
+    for (int j = 0; j < 4; j++) {
+      v[2 * j] = __uint_as_float(w[j] << 16);
+      v[2 * j + 1] = __uint_as_float(w[j] & 0xFFFF0000u);
     }
+  }
+  __device__ static void load_tail(const void* x, uint64_t i, uint64_t n, float* v) {
+    const uint16_t* p = static_cast<const uint16_t*>(x);
+    for (int j = 0; j < 8 * kQuantVec; j++) v[j] = i + j < n ? __uint_as_float((uint32_t)p[i + j] << 16) : 0.0f;
   }
 };
 
+__device__ __forceinline__ void q_cp_async16(uint32_t smem, const void* g, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q cp.async.cg.shared.global [%0], [%1], 16;\n\t}" ::"r"(smem),
+      "l"(g), "r"((uint32_t)pred)
+      : "memory");
+}
+__device__ __forceinline__ void q_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void q_cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Steps per launch: step indices and their products stay in 32 bits.
+constexpr uint64_t kQuantMaxSteps = 1ull << 30;
+
+// Input pipeline: warp step s covers elements [s kStep, (s + 1) kStep),
+// 1 KiB of input, 32 contiguous bytes per lane; warps take steps s = first,
+// first + W, ... (W warps in the grid).  A warp keeps its next
+// kQuantDepth - 1 steps in flight: its k-th step goes by cp.async into its
+// 1 KiB of shared slot k mod kQuantDepth, each copy instruction 512
+// contiguous bytes (one commit group per step; in a ragged last step only
+// the 16-byte vectors wholly inside are copied).  About 100 bytes per thread
+// are in flight without holding registers.  Lanes read bytes other lanes
+// copied, so each step starts with the lane's wait on its own groups and a
+// warp barrier; a slot is refilled after that barrier, when every lane has
+// finished the step that read it.  A lane whose 32 bytes are not wholly
+// inside reads its elements with plain loads.
 template <int kDtype>
 __global__ void __launch_bounds__(kQuantThreads)
 quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ codes, float* __restrict__ scales,
                 unsigned long long* __restrict__ hist, uint32_t* __restrict__ status) {
-  constexpr int E = QuantIo<kDtype>::kPerLane;  // elements per lane
+  constexpr int E = QuantIo<kDtype>::kPerVec * kQuantVec;  // elements per lane
   constexpr int kLanesPerBlock = 32 / E;
-  constexpr uint64_t kStep = 32 * E;             // elements per warp step
+  constexpr uint32_t kStep = 32 * E;             // elements per warp step
+  constexpr uint32_t kWords = E / 4;             // code words per lane
   __shared__ uint32_t sh[kQuantWarps][257];
+  __shared__ uint4 ring[kQuantDepth][kQuantWarps][kQuantVec * 32];
   if (hist) {
     for (int i = threadIdx.x; i < kQuantWarps * 257; i += kQuantThreads) (&sh[0][0])[i] = 0;
     __syncthreads();
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* my = sh[warp];
-  const uint64_t n_steps = (n + kStep - 1) / kStep;
-  const uint64_t warps = (uint64_t)gridDim.x * kQuantWarps;
-  bool bad = false;
-  for (uint64_t s0 = (uint64_t)blockIdx.x * kQuantWarps + warp; s0 < n_steps; s0 += warps * kQuantUnroll) {
-    float v[kQuantUnroll][E];
+  const uint32_t n_steps = (uint32_t)((n + kStep - 1) / kStep);  // <= kQuantMaxSteps
+  const uint32_t warps = gridDim.x * kQuantWarps;
+  const uint32_t first = blockIdx.x * kQuantWarps + warp;
+  const uint32_t cnt = first < n_steps ? (n_steps - first + warps - 1) / warps : 0;  // this warp's steps
+  // steps whose 32 bytes of this lane (nf), whose whole 1 KiB (nfw), lie
+  // wholly inside: all but a ragged last
+  const bool ragged_last = cnt > 0 && first + (cnt - 1) * warps == n_steps - 1;
+  const uint32_t nfw = ragged_last && (uint64_t)n_steps * kStep > n ? cnt - 1 : cnt;
+  const uint32_t nf = ragged_last && (uint64_t)(n_steps - 1) * kStep + (uint64_t)(lane + 1) * E > n ? cnt - 1 : cnt;
+  const uint64_t n_bytes = n * (16 / QuantIo<kDtype>::kPerVec);
+  uint8_t* c_lane = codes + lane * E;
+  const bool scale_lane = lane % kLanesPerBlock == 0;
+  // copy instruction u of lane l: bytes [512 u + 16 l, + 16) of the step
+  const uint8_t* x_copy = static_cast<const uint8_t*>(x) + lane * 16;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(&ring[0][warp][lane]);
+  auto fetch = [&](uint32_t k) {  // step k of this warp into slot k mod kQuantDepth
+    const uint64_t b = (uint64_t)(first + k * warps) * (512u * kQuantVec);
+    const uint32_t d = ring_s + (k % kQuantDepth) * (kQuantWarps * kQuantVec * 512u);
 #pragma unroll
-    for (int u = 0; u < kQuantUnroll; u++) {
-      const uint64_t s = s0 + u * warps;
-      const uint64_t i = s * kStep + (uint64_t)lane * E;
-      if (s < n_steps && i < n) {
-        QuantIo<kDtype>::load(x, i, n, v[u]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < E; j++) v[u][j] = 0.0f;
-      }
+    for (int u = 0; u < kQuantVec; u++) {
+      const bool in = k < nfw || (k == nfw && k < cnt && b + lane * 16 + 512u * u + 16 <= n_bytes);
+      q_cp_async16(d + 512u * u, in && QLC_GUARD(b + lane * 16 + 512u * u + 16 <= n_bytes, status)
+                                     ? x_copy + b + 512u * u : x_copy, in);
     }
+    q_cp_async_commit();
+  };
 #pragma unroll
-    for (int u = 0; u < kQuantUnroll; u++) {
-      const uint64_t s = s0 + u * warps;
-      if (s >= n_steps) break;  // warp-uniform
-      const uint64_t i = s * kStep + (uint64_t)lane * E;
-      float amax = 0.0f;
+  for (uint32_t d = 0; d + 1 < kQuantDepth; d++) fetch(d);
+  bool bad = false;
+  uint32_t s = first;
+  for (uint32_t k = 0; k < cnt; k++, s += warps) {
+    // groups committed so far: kQuantDepth - 1 + k; step k's is complete
+    // when at most kQuantDepth - 2 are pending
+    q_cp_async_wait<kQuantDepth - 2>();
+    __syncwarp();
+    fetch(k + kQuantDepth - 1);  // into the slot step k - 1 was read from
+    const uint64_t i = (uint64_t)s * kStep + (uint64_t)lane * E;
+    const bool full = k < nf;
+    float v[E];
+    if (full) {
+      const uint4* r = &ring[k % kQuantDepth][warp][lane * kQuantVec];
 #pragma unroll
-      for (int j = 0; j < E; j++) {
-        bad |= !isfinite(v[u][j]);
-        amax = fmaxf(amax, fabsf(v[u][j]));
-      }
+      for (int u = 0; u < kQuantVec; u++) QuantIo<kDtype>::unpack(r[u], v + u * QuantIo<kDtype>::kPerVec);
+    } else {
+      QuantIo<kDtype>::load_tail(x, i, n, v);  // zeros past the end
+    }
+    float amax = 0.0f;
 #pragma unroll
-      for (int o = 1; o < kLanesPerBlock; o <<= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-      const float scale = amax / 480.0f;
-      // one reciprocal per lane and block; a scale below 2^-125 (whose
-      // reciprocal could overflow) takes the exact division for every element
-      const float y = 1.0f / scale;
-      const bool by_product = scale >= 0x1p-125f;
-      uint32_t c[E];
-      bool exact = !by_product;
+    for (int j = 0; j < E; j++) amax = fmax_nan(amax, fabsf(v[j]));
+    bad |= !(amax <= 3.402823466e38f);  // NaN or infinity in this lane
 #pragma unroll
-      for (int j = 0; j < E; j++) {
-        bool near;
-        c[j] = e4m3_rne_or_near(v[u][j] * y, &near);
-        exact |= near;
-      }
-      if (!(scale > 0.0f)) {
+    for (int o = 1; o < kLanesPerBlock; o <<= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float scale = amax / 480.0f;
+    // one reciprocal per lane and block, within 2 ulp for scale in
+    // [2^-126, 2^126]; a scale below 2^-125 takes the exact division for
+    // every element
+    const float y = __fdividef(1.0f, scale);
+    uint32_t w[kWords], diff = scale >= 0x1p-125f ? 0u : 1u;
 #pragma unroll
-        for (int j = 0; j < E; j++) c[j] = 0u;
-      } else if (exact) {  // rare: one branch per lane and block
+    for (int t = 0; t < (int)kWords; t++) {
+      const uint32_t lo = e4m3x2_bracket(v[4 * t] * y, v[4 * t + 1] * y, &diff);
+      const uint32_t hi = e4m3x2_bracket(v[4 * t + 2] * y, v[4 * t + 3] * y, &diff);
+      w[t] = __byte_perm(lo, hi, 0x5410);
+    }
+    if (!(scale > 0.0f)) {
 #pragma unroll
-        for (int j = 0; j < E; j++) c[j] = e4m3_rne(v[u][j] / scale);
-      }
-      if (i < n && (lane % kLanesPerBlock) == 0 && QLC_GUARD(i / 32 < (n + 31) / 32, status)) scales[i / 32] = scale;
-      if (i + E <= n) {
-        if (E == 4) {
-          *reinterpret_cast<uint32_t*>(codes + i) = c[0] | c[1] << 8 | c[2] << 16 | c[3] << 24;
-        } else {
-          *reinterpret_cast<uint2*>(codes + i) =
-              make_uint2(c[0] | c[1] << 8 | c[2] << 16 | c[3] << 24, c[4] | c[5] << 8 | c[6] << 16 | c[7] << 24);
-        }
-        if (hist) {
+      for (int t = 0; t < (int)kWords; t++) w[t] = 0u;
+    } else if (diff != 0u) {  // rare: one branch per lane and block
 #pragma unroll
-          for (int j = 0; j < E; j++)
-            if (QLC_GUARD(c[j] < 256u, status)) atomicAdd(&my[c[j] + (c[j] >> 7)], 1u);
-        }
-      } else {
+      for (int t = 0; t < (int)kWords; t++)
+        w[t] = e4m3_rne(v[4 * t] / scale) | e4m3_rne(v[4 * t + 1] / scale) << 8 |
+               e4m3_rne(v[4 * t + 2] / scale) << 16 | e4m3_rne(v[4 * t + 3] / scale) << 24;
+    }
+    if (scale_lane && i < n && QLC_GUARD(i / 32 < (n + 31) / 32, status)) scales[i / 32] = scale;
+    if (full && QLC_GUARD(i + E <= n, status)) {
+      if constexpr (kWords == 2)
+        *reinterpret_cast<uint2*>(c_lane + (uint64_t)s * kStep) = make_uint2(w[0], w[1]);
+      else
+        *reinterpret_cast<uint4*>(c_lane + (uint64_t)s * kStep) = make_uint4(w[0], w[1], w[2], w[3]);
+      if (hist) {
+#pragma unroll
         for (int j = 0; j < E; j++) {
-          if (i + j < n) {
-            codes[i + j] = (uint8_t)c[j];
-            if (hist && QLC_GUARD(c[j] < 256u, status)) atomicAdd(&my[c[j] + (c[j] >> 7)], 1u);
-          }
+          const uint32_t c = __byte_perm(w[j / 4], 0, 0x4440 + (j % 4));
+          atomicAdd(&my[c + (c >> 7)], 1u);
+        }
+      }
+    } else {
+      for (int j = 0; j < E; j++) {
+        if (i + j < n) {
+          const uint32_t c = (w[j / 4] >> (8 * (j % 4))) & 0xFFu;
+          codes[i + j] = (uint8_t)c;
+          if (hist) atomicAdd(&my[c + (c >> 7)], 1u);
         }
       }
     }
   }
+  q_cp_async_wait<0>();
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(status, QLC_ERR_ARG);
   if (hist) {
     for (int b = threadIdx.x; b < 256; b += kQuantThreads) {
@@ -247,6 +321,28 @@ dequantize_kernel(const uint8_t* __restrict__ codes, const float* __restrict__ s
 
 }  // namespace qlc
 
+namespace qlc {
+// Resident quantiser CTAs per SM (the occupancy calculator's figure, cached
+// per device below 64 and dtype; at least 1).
+static int quant_ctas_per_sm(qlc_dtype dtype) {
+  static std::atomic<int> cached[64][2];
+  const int k = dtype == QLC_DTYPE_F32 ? 0 : 1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 64;
+  if (dev < 64) {
+    const int c = cached[dev][k].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int v = 0;
+  const cudaError_t e =
+      k == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, quantize_kernel<QLC_DTYPE_F32>, kQuantThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, quantize_kernel<QLC_DTYPE_BF16>, kQuantThreads, 0);
+  if (e != cudaSuccess || v <= 0) v = 1;
+  if (dev < 64) cached[dev][k].store(v, std::memory_order_relaxed);
+  return v;
+}
+}  // namespace qlc
+
 using namespace qlc;
 
 extern "C" qlc_status qlc_quantize_e4m3(const void* d_x, qlc_dtype dtype, size_t n, uint8_t* d_codes,
@@ -262,15 +358,26 @@ extern "C" qlc_status qlc_quantize_e4m3(const void* d_x, qlc_dtype dtype, size_t
   if (d_hist && !accumulate && cudaMemsetAsync(d_hist, 0, 256 * sizeof(uint64_t), st) != cudaSuccess)
     return QLC_ERR_CUDA;
   if (n == 0) return QLC_OK;
-  const uint64_t per_cta = (uint64_t)kQuantThreads * (dtype == QLC_DTYPE_F32 ? 4 : 8) * kQuantUnroll;
-  const uint64_t want = (n + per_cta - 1) / per_cta;
-  const uint64_t cap = (uint64_t)sm_count() * 8;
-  const int grid = (int)(want < cap ? want : cap);
+  // one resident wave: each CTA loops over its steps with its copies in
+  // flight; inputs above kQuantMaxSteps steps go in several launches (slices
+  // of whole blocks, the histogram accumulating)
+  const uint64_t step = (uint64_t)32 * kQuantVec * (dtype == QLC_DTYPE_F32 ? 4 : 8);  // elements per warp step
+  const uint64_t elem = dtype == QLC_DTYPE_F32 ? 4 : 2;
+  const uint64_t slice = kQuantMaxSteps * step;
+  const uint64_t cap = (uint64_t)sm_count() * quant_ctas_per_sm(dtype);
   unsigned long long* h = reinterpret_cast<unsigned long long*>(d_hist);
-  if (dtype == QLC_DTYPE_F32)
-    quantize_kernel<QLC_DTYPE_F32><<<grid, kQuantThreads, 0, st>>>(d_x, n, d_codes, d_scales, h, d_status);
-  else
-    quantize_kernel<QLC_DTYPE_BF16><<<grid, kQuantThreads, 0, st>>>(d_x, n, d_codes, d_scales, h, d_status);
+  for (uint64_t off = 0; off < n; off += slice) {
+    const uint64_t m = n - off < slice ? n - off : slice;
+    const uint64_t want = (m + step * kQuantWarps - 1) / (step * kQuantWarps);
+    const int grid = (int)(want < cap ? want : cap);
+    const void* xs = static_cast<const uint8_t*>(d_x) + off * elem;
+    if (dtype == QLC_DTYPE_F32)
+      quantize_kernel<QLC_DTYPE_F32><<<grid, kQuantThreads, 0, st>>>(xs, m, d_codes + off, d_scales + off / 32, h,
+                                                                     d_status);
+    else
+      quantize_kernel<QLC_DTYPE_BF16><<<grid, kQuantThreads, 0, st>>>(xs, m, d_codes + off, d_scales + off / 32, h,
+                                                                      d_status);
+  }
   return cudaGetLastError() == cudaSuccess ? QLC_OK : QLC_ERR_CUDA;
 }
 
