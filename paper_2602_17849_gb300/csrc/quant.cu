@@ -54,25 +54,22 @@ __device__ __forceinline__ uint32_t e4m3_rne(float v) {
 // the FMA pipe: (|v| - 464) 2^20 clamped to [0, 1] is 1.0 above 464 (the
 // fp32 neighbours of 464 are 2^-15 away) and 0.0 up to it, and
 // f0 + 256 f1 + 2^23 holds the two flags in its low bits, one per byte.
-// Returns the upper side's codes (qa | qb << 8); the two sides' differences,
-// flags included, are ORed into *diff: nonzero means the caller takes the
-// exact division.
+// Gives both sides' codes (qa | qb << 8): where a byte differs the caller
+// takes the exact division for that element.
 __device__ __forceinline__ uint32_t sat_flags(float a, float b) {
   const float fa = __saturatef(fmaf(fabsf(a), 0x1p20f, -464.0f * 0x1p20f));
   const float fb = __saturatef(fmaf(fabsf(b), 0x1p20f, -464.0f * 0x1p20f));
   return __float_as_uint(fmaf(fb, 256.0f, fa + 0x1p23f));
 }
-__device__ __forceinline__ uint32_t e4m3x2_bracket(float qa, float qb, uint32_t* diff) {
+__device__ __forceinline__ void e4m3x2_bracket(float qa, float qb, uint32_t* up, uint32_t* lo) {
   constexpr float d = 0x1p-20f;
   const float ua = fmaf(qa, d, qa), ub = fmaf(qb, d, qb);  // the larger magnitudes
   const float la = fmaf(qa, -d, qa), lb = fmaf(qb, -d, qb);
   uint16_t cu, cl;
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(cu) : "f"(ub), "f"(ua));
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(cl) : "f"(lb), "f"(la));
-  const uint32_t up = (uint32_t)cu | (sat_flags(ua, ub) & 0x0101u);  // 0x7E -> 0x7F above 464
-  const uint32_t lo = (uint32_t)cl | (sat_flags(la, lb) & 0x0101u);
-  *diff |= up ^ lo;
-  return up;
+  *up = (uint32_t)cu | (sat_flags(ua, ub) & 0x0101u);  // 0x7E -> 0x7F above 464
+  *lo = (uint32_t)cl | (sat_flags(la, lb) & 0x0101u);
 }
 
 // max(a, b) that returns NaN when either is NaN.
@@ -215,21 +212,33 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
     // [2^-126, 2^126]; a scale below 2^-125 takes the exact division for
     // every element
     const float y = __fdividef(1.0f, scale);
-    uint32_t w[kWords], diff = scale >= 0x1p-125f ? 0u : 1u;
+    // w: the codes; dw: nonzero bytes mark the elements whose code the
+    // bracket leaves open (all of them for a scale below 2^-125)
+    uint32_t w[kWords], dw[kWords], open = 0u;
+    const uint32_t all = scale >= 0x1p-125f ? 0u : ~0u;
 #pragma unroll
     for (int t = 0; t < (int)kWords; t++) {
-      const uint32_t lo = e4m3x2_bracket(v[4 * t] * y, v[4 * t + 1] * y, &diff);
-      const uint32_t hi = e4m3x2_bracket(v[4 * t + 2] * y, v[4 * t + 3] * y, &diff);
-      w[t] = __byte_perm(lo, hi, 0x5410);
+      uint32_t u0, l0, u1, l1;
+      e4m3x2_bracket(v[4 * t] * y, v[4 * t + 1] * y, &u0, &l0);
+      e4m3x2_bracket(v[4 * t + 2] * y, v[4 * t + 3] * y, &u1, &l1);
+      w[t] = __byte_perm(u0, u1, 0x5410);
+      dw[t] = (w[t] ^ __byte_perm(l0, l1, 0x5410)) | all;
+      open |= dw[t];
     }
     if (!(scale > 0.0f)) {
 #pragma unroll
       for (int t = 0; t < (int)kWords; t++) w[t] = 0u;
-    } else if (diff != 0u) {  // rare: one branch per lane and block
+    } else if (open != 0u) {  // rare: the open elements alone take the exact division
 #pragma unroll
-      for (int t = 0; t < (int)kWords; t++)
-        w[t] = e4m3_rne(v[4 * t] / scale) | e4m3_rne(v[4 * t + 1] / scale) << 8 |
-               e4m3_rne(v[4 * t + 2] / scale) << 16 | e4m3_rne(v[4 * t + 3] / scale) << 24;
+      for (int t = 0; t < (int)kWords; t++) {
+        while (dw[t] != 0u) {
+          const uint32_t sh = (uint32_t)(__ffs(dw[t]) - 1) & ~7u;  // bit 0 of the byte
+          const uint32_t jb = sh >> 3;
+          const float vj = jb == 0 ? v[4 * t] : jb == 1 ? v[4 * t + 1] : jb == 2 ? v[4 * t + 2] : v[4 * t + 3];
+          w[t] = (w[t] & ~(0xFFu << sh)) | (e4m3_rne(vj / scale) << sh);
+          dw[t] &= ~(0xFFu << sh);
+        }
+      }
     }
     if (scale_lane && i < n && QLC_GUARD(i / 32 < (n + 31) / 32, status)) scales[i / 32] = scale;
     if (full && QLC_GUARD(i + E <= n, status)) {

@@ -34,6 +34,12 @@ def _floats(n, seed):
     if n >= 160:
         x[96:128] = torch.tensor(2.0 ** -140)                 # subnormal scale
         x[128:160] = torch.tensor([2.0 ** -10, -(2.0 ** -10), 7.5, 480.0] * 8)  # ties, extremes
+    if n >= 256:
+        # scale 1: the saturation midpoint 464 and its fp32 neighbours, 448, 480
+        x[160:192] = torch.tensor([480.0, 464.0, -464.0, 463.99997, 464.00003, 448.0, -480.0, 232.0] * 4)
+        # scales just above and below 2^-125, where the kernel switches to the exact division
+        x[192:224] = torch.tensor([480.0 * 2.0 ** -125 * 1.0000001, 3.0 * 2.0 ** -126, -(2.0 ** -120), 0.0] * 8)
+        x[224:256] = torch.tensor([480.0 * 2.0 ** -125 * 0.9999999, 464.0 * 2.0 ** -125, 2.0 ** -130, 1e-40] * 8)
     return x
 
 
