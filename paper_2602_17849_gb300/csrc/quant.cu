@@ -127,6 +127,56 @@ __device__ __forceinline__ void q_cp_async_wait() {
 // Steps per launch: step indices and their products stay in 32 bits.
 constexpr uint64_t kQuantMaxSteps = 1ull << 30;
 
+// Scale and codes of one lane's E elements v (its block of 32 spans
+// 32 / E lanes, whose absmax the shuffles combine).  Sets bad for NaN or
+// infinity among v.  w receives the codes, 4 per word, element 4t + b in
+// byte b of w[t].
+template <int E>
+__device__ __forceinline__ float lane_codes(const float (&v)[E], uint32_t (&w)[E / 4], bool& bad) {
+  constexpr int kLanesPerBlock = 32 / E;
+  constexpr int kWords = E / 4;
+  float amax = 0.0f;
+#pragma unroll
+  for (int j = 0; j < E; j++) amax = fmax_nan(amax, fabsf(v[j]));
+  bad |= !(amax <= 3.402823466e38f);  // NaN or infinity in this lane
+#pragma unroll
+  for (int o = 1; o < kLanesPerBlock; o <<= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  const float scale = amax / 480.0f;
+  // one reciprocal per lane and block, within 2 ulp for scale in
+  // [2^-126, 2^126]; a scale below 2^-125 takes the exact division for
+  // every element
+  const float y = __fdividef(1.0f, scale);
+  // dw: nonzero bytes mark the elements whose code the bracket leaves open
+  // (all of them for a scale below 2^-125)
+  uint32_t dw[kWords], open = 0u;
+  const uint32_t all = scale >= 0x1p-125f ? 0u : ~0u;
+#pragma unroll
+  for (int t = 0; t < kWords; t++) {
+    uint32_t u0, l0, u1, l1;
+    e4m3x2_bracket(v[4 * t] * y, v[4 * t + 1] * y, &u0, &l0);
+    e4m3x2_bracket(v[4 * t + 2] * y, v[4 * t + 3] * y, &u1, &l1);
+    w[t] = __byte_perm(u0, u1, 0x5410);
+    dw[t] = (w[t] ^ __byte_perm(l0, l1, 0x5410)) | all;
+    open |= dw[t];
+  }
+  if (!(scale > 0.0f)) {
+#pragma unroll
+    for (int t = 0; t < kWords; t++) w[t] = 0u;
+  } else if (open != 0u) {  // rare: the open elements alone take the exact division
+#pragma unroll
+    for (int t = 0; t < kWords; t++) {
+      while (dw[t] != 0u) {
+        const uint32_t sh = (uint32_t)(__ffs(dw[t]) - 1) & ~7u;  // bit 0 of the byte
+        const uint32_t jb = sh >> 3;
+        const float vj = jb == 0 ? v[4 * t] : jb == 1 ? v[4 * t + 1] : jb == 2 ? v[4 * t + 2] : v[4 * t + 3];
+        w[t] = (w[t] & ~(0xFFu << sh)) | (e4m3_rne(vj / scale) << sh);
+        dw[t] &= ~(0xFFu << sh);
+      }
+    }
+  }
+  return scale;
+}
+
 // Input pipeline: warp step s covers elements [s kStep, (s + 1) kStep),
 // 1 KiB of input, 32 contiguous bytes per lane; warps take steps s = first,
 // first + W, ... (W warps in the grid).  A warp keeps its next
@@ -137,8 +187,9 @@ constexpr uint64_t kQuantMaxSteps = 1ull << 30;
 // are in flight without holding registers.  Lanes read bytes other lanes
 // copied, so each step starts with the lane's wait on its own groups and a
 // warp barrier; a slot is refilled after that barrier, when every lane has
-// finished the step that read it.  A lane whose 32 bytes are not wholly
-// inside reads its elements with plain loads.
+// finished the step that read it.  Every step but a ragged last one takes
+// the short path; there a lane whose 32 bytes are not wholly inside reads
+// its elements with plain loads.
 template <int kDtype>
 __global__ void __launch_bounds__(kQuantThreads)
 quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ codes, float* __restrict__ scales,
@@ -147,6 +198,7 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
   constexpr int kLanesPerBlock = 32 / E;
   constexpr uint32_t kStep = 32 * E;             // elements per warp step
   constexpr uint32_t kWords = E / 4;             // code words per lane
+  constexpr uint32_t kSlot = kQuantWarps * kQuantVec * 512u;  // bytes of a ring slot
   __shared__ uint32_t sh[kQuantWarps][257];
   __shared__ uint4 ring[kQuantDepth][kQuantWarps][kQuantVec * 32];
   if (hist) {
@@ -159,109 +211,85 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
   const uint32_t warps = gridDim.x * kQuantWarps;
   const uint32_t first = blockIdx.x * kQuantWarps + warp;
   const uint32_t cnt = first < n_steps ? (n_steps - first + warps - 1) / warps : 0;  // this warp's steps
-  // steps whose 32 bytes of this lane (nf), whose whole 1 KiB (nfw), lie
-  // wholly inside: all but a ragged last
-  const bool ragged_last = cnt > 0 && first + (cnt - 1) * warps == n_steps - 1;
-  const uint32_t nfw = ragged_last && (uint64_t)n_steps * kStep > n ? cnt - 1 : cnt;
-  const uint32_t nf = ragged_last && (uint64_t)(n_steps - 1) * kStep + (uint64_t)(lane + 1) * E > n ? cnt - 1 : cnt;
+  // this warp's steps whose whole 1 KiB lies inside: all but a ragged last
+  const uint32_t nfw = cnt > 0 && first + (cnt - 1) * warps == n_steps - 1 && (uint64_t)n_steps * kStep > n
+                           ? cnt - 1 : cnt;
   const uint64_t n_bytes = n * (16 / QuantIo<kDtype>::kPerVec);
   uint8_t* c_lane = codes + lane * E;
+  float* s_lane = scales + lane / kLanesPerBlock;
   const bool scale_lane = lane % kLanesPerBlock == 0;
   // copy instruction u of lane l: bytes [512 u + 16 l, + 16) of the step
   const uint8_t* x_copy = static_cast<const uint8_t*>(x) + lane * 16;
   const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(&ring[0][warp][lane]);
   auto fetch = [&](uint32_t k) {  // step k of this warp into slot k mod kQuantDepth
+    const uint32_t d = ring_s + (k % kQuantDepth) * kSlot;
     const uint64_t b = (uint64_t)(first + k * warps) * (512u * kQuantVec);
-    const uint32_t d = ring_s + (k % kQuantDepth) * (kQuantWarps * kQuantVec * 512u);
+    if (k < nfw) {
 #pragma unroll
-    for (int u = 0; u < kQuantVec; u++) {
-      const bool in = k < nfw || (k == nfw && k < cnt && b + lane * 16 + 512u * u + 16 <= n_bytes);
-      q_cp_async16(d + 512u * u, in && QLC_GUARD(b + lane * 16 + 512u * u + 16 <= n_bytes, status)
-                                     ? x_copy + b + 512u * u : x_copy, in);
+      for (int u = 0; u < kQuantVec; u++)
+        q_cp_async16(d + 512u * u, x_copy + b + 512u * u,
+                     QLC_GUARD(b + lane * 16 + 512u * u + 16 <= n_bytes, status));
+    } else if (k < cnt) {  // the ragged last step: the vectors wholly inside
+#pragma unroll
+      for (int u = 0; u < kQuantVec; u++) {
+        const bool in = b + lane * 16 + 512u * u + 16 <= n_bytes;
+        q_cp_async16(d + 512u * u, in ? x_copy + b + 512u * u : x_copy, in);
+      }
     }
     q_cp_async_commit();
+  };
+  auto count = [&](const uint32_t (&w)[kWords], int m) {  // the first m codes into the histogram
+#pragma unroll
+    for (int j = 0; j < E; j++) {
+      if (j < m) {
+        const uint32_t c = __byte_perm(w[j / 4], 0, 0x4440 + (j % 4));
+        atomicAdd(&my[c + (c >> 7)], 1u);
+      }
+    }
   };
 #pragma unroll
   for (uint32_t d = 0; d + 1 < kQuantDepth; d++) fetch(d);
   bool bad = false;
-  uint32_t s = first;
-  for (uint32_t k = 0; k < cnt; k++, s += warps) {
+  uint32_t s = first, k = 0;
+  for (; k < nfw; k++, s += warps) {
     // groups committed so far: kQuantDepth - 1 + k; step k's is complete
     // when at most kQuantDepth - 2 are pending
     q_cp_async_wait<kQuantDepth - 2>();
     __syncwarp();
     fetch(k + kQuantDepth - 1);  // into the slot step k - 1 was read from
-    const uint64_t i = (uint64_t)s * kStep + (uint64_t)lane * E;
-    const bool full = k < nf;
     float v[E];
-    if (full) {
+    const uint4* r = &ring[k % kQuantDepth][warp][lane * kQuantVec];
+#pragma unroll
+    for (int u = 0; u < kQuantVec; u++) QuantIo<kDtype>::unpack(r[u], v + u * QuantIo<kDtype>::kPerVec);
+    uint32_t w[kWords];
+    const float scale = lane_codes<E>(v, w, bad);
+    if (scale_lane && QLC_GUARD((uint64_t)s * kStep + lane * E < n, status)) s_lane[(uint64_t)s * (kStep / 32)] = scale;
+    if (QLC_GUARD((uint64_t)s * kStep + (lane + 1) * E <= n, status)) {
+      if constexpr (kWords == 2)
+        *reinterpret_cast<uint2*>(c_lane + (uint64_t)s * kStep) = make_uint2(w[0], w[1]);
+      else
+        *reinterpret_cast<uint4*>(c_lane + (uint64_t)s * kStep) = make_uint4(w[0], w[1], w[2], w[3]);
+      if (hist) count(w, E);
+    }
+  }
+  if (k < cnt) {  // the ragged last step
+    q_cp_async_wait<0>();
+    __syncwarp();
+    const uint64_t i = (uint64_t)s * kStep + (uint64_t)lane * E;
+    float v[E];
+    if (i + E <= n) {
       const uint4* r = &ring[k % kQuantDepth][warp][lane * kQuantVec];
 #pragma unroll
       for (int u = 0; u < kQuantVec; u++) QuantIo<kDtype>::unpack(r[u], v + u * QuantIo<kDtype>::kPerVec);
     } else {
       QuantIo<kDtype>::load_tail(x, i, n, v);  // zeros past the end
     }
-    float amax = 0.0f;
-#pragma unroll
-    for (int j = 0; j < E; j++) amax = fmax_nan(amax, fabsf(v[j]));
-    bad |= !(amax <= 3.402823466e38f);  // NaN or infinity in this lane
-#pragma unroll
-    for (int o = 1; o < kLanesPerBlock; o <<= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-    const float scale = amax / 480.0f;
-    // one reciprocal per lane and block, within 2 ulp for scale in
-    // [2^-126, 2^126]; a scale below 2^-125 takes the exact division for
-    // every element
-    const float y = __fdividef(1.0f, scale);
-    // w: the codes; dw: nonzero bytes mark the elements whose code the
-    // bracket leaves open (all of them for a scale below 2^-125)
-    uint32_t w[kWords], dw[kWords], open = 0u;
-    const uint32_t all = scale >= 0x1p-125f ? 0u : ~0u;
-#pragma unroll
-    for (int t = 0; t < (int)kWords; t++) {
-      uint32_t u0, l0, u1, l1;
-      e4m3x2_bracket(v[4 * t] * y, v[4 * t + 1] * y, &u0, &l0);
-      e4m3x2_bracket(v[4 * t + 2] * y, v[4 * t + 3] * y, &u1, &l1);
-      w[t] = __byte_perm(u0, u1, 0x5410);
-      dw[t] = (w[t] ^ __byte_perm(l0, l1, 0x5410)) | all;
-      open |= dw[t];
-    }
-    if (!(scale > 0.0f)) {
-#pragma unroll
-      for (int t = 0; t < (int)kWords; t++) w[t] = 0u;
-    } else if (open != 0u) {  // rare: the open elements alone take the exact division
-#pragma unroll
-      for (int t = 0; t < (int)kWords; t++) {
-        while (dw[t] != 0u) {
-          const uint32_t sh = (uint32_t)(__ffs(dw[t]) - 1) & ~7u;  // bit 0 of the byte
-          const uint32_t jb = sh >> 3;
-          const float vj = jb == 0 ? v[4 * t] : jb == 1 ? v[4 * t + 1] : jb == 2 ? v[4 * t + 2] : v[4 * t + 3];
-          w[t] = (w[t] & ~(0xFFu << sh)) | (e4m3_rne(vj / scale) << sh);
-          dw[t] &= ~(0xFFu << sh);
-        }
-      }
-    }
+    uint32_t w[kWords];
+    const float scale = lane_codes<E>(v, w, bad);
     if (scale_lane && i < n && QLC_GUARD(i / 32 < (n + 31) / 32, status)) scales[i / 32] = scale;
-    if (full && QLC_GUARD(i + E <= n, status)) {
-      if constexpr (kWords == 2)
-        *reinterpret_cast<uint2*>(c_lane + (uint64_t)s * kStep) = make_uint2(w[0], w[1]);
-      else
-        *reinterpret_cast<uint4*>(c_lane + (uint64_t)s * kStep) = make_uint4(w[0], w[1], w[2], w[3]);
-      if (hist) {
-#pragma unroll
-        for (int j = 0; j < E; j++) {
-          const uint32_t c = __byte_perm(w[j / 4], 0, 0x4440 + (j % 4));
-          atomicAdd(&my[c + (c >> 7)], 1u);
-        }
-      }
-    } else {
-      for (int j = 0; j < E; j++) {
-        if (i + j < n) {
-          const uint32_t c = (w[j / 4] >> (8 * (j % 4))) & 0xFFu;
-          codes[i + j] = (uint8_t)c;
-          if (hist) atomicAdd(&my[c + (c >> 7)], 1u);
-        }
-      }
-    }
+    for (int j = 0; j < E; j++)
+      if (i + j < n) codes[i + j] = (uint8_t)(w[j / 4] >> (8 * (j % 4)));
+    if (hist && i < n) count(w, (int)(n - i < (uint64_t)E ? n - i : E));
   }
   q_cp_async_wait<0>();
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(status, QLC_ERR_ARG);
