@@ -304,40 +304,7 @@ __device__ __forceinline__ void st_cs_32(uint8_t* dst, const uint32_t w[8], bool
   }
 }
 
-// Sixteen decoded symbols v of one chunk, starting at symbol index i of the
-// tensor (a multiple of 16), to their destination.
-template <int kOut>
-__device__ __forceinline__ void put16(void* out, const float* scales, uint64_t i, uint4 v) {
-  if (kOut == kOutCodes) {
-    // streaming store: the output is written once
-    asm volatile("st.global.cs.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(static_cast<uint8_t*>(out) + i), "r"(v.x),
-                 "r"(v.y), "r"(v.z), "r"(v.w)
-                 : "memory");
-  } else {
-    const float sc = scales[i / 32];
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-    float y[16];
-#pragma unroll
-    for (int j = 0; j < 16; j++) y[j] = e4m3_to_f32((w[j >> 2] >> (8 * (j & 3))) & 0xFFu) * sc;
-    if (kOut == QLC_DTYPE_F32) {
-      float4* o = reinterpret_cast<float4*>(static_cast<float*>(out) + i);
-#pragma unroll
-      for (int k = 0; k < 4; k++) __stcs(o + k, make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]));
-    } else {
-      uint32_t p[8];
-#pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const __nv_bfloat162 hb = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
-        p[k] = *reinterpret_cast<const uint32_t*>(&hb);
-      }
-      uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + i);
-      __stcs(o, make_uint4(p[0], p[1], p[2], p[3]));
-      __stcs(o + 1, make_uint4(p[4], p[5], p[6], p[7]));
-    }
-  }
-}
-
-// Fewer than 16 symbols (a tensor's ragged end).
+// Single symbols (ragged chunk ends).
 template <int kOut>
 __device__ __forceinline__ void put_tail(void* out, const float* scales, uint64_t i, const uint8_t* sb,
                                          uint32_t cnt) {
@@ -355,20 +322,19 @@ __device__ __forceinline__ void put_tail(void* out, const float* scales, uint64_
 }
 
 // Thirty-two decoded symbols w of one chunk, starting at symbol index i of
-// the tensor (a multiple of 32), to their destination.
+// the tensor (a multiple of 32), to their destination; sc is their block's
+// scale (dequantising outputs).
 template <int kOut>
-__device__ __forceinline__ void put32(void* out, const float* scales, uint64_t i, const uint32_t w[8],
-                                      bool aligned32) {
+__device__ __forceinline__ void put32(void* out, float sc, uint64_t i, const uint32_t w[8], bool aligned32) {
   if (kOut == kOutCodes) {
     st_cs_32(static_cast<uint8_t*>(out) + i, w, aligned32);
   } else {
     // the block's 32 values share one scale (i is a multiple of 32); they go
     // out in whole 32-byte sectors: 4 stores of 8 fp32, or 2 of 16 bf16
-    const float sc = scales[i / 32];
     uint32_t v[kOut == QLC_DTYPE_F32 ? 32 : 16];
 #pragma unroll
     for (int j = 0; j < 32; j++) {
-      const float y = e4m3_to_f32((w[j >> 2] >> (8 * (j & 3))) & 0xFFu) * sc;
+      const float y = __uint_as_float(e4m3_scaled_bits(w[j >> 2], j & 3)) * 0x1p120f * sc;
       if (kOut == QLC_DTYPE_F32) {
         v[j] = __float_as_uint(y);
       } else if (j & 1) {
@@ -396,7 +362,7 @@ __device__ __forceinline__ void put1(void* out, const float* scales, uint64_t i,
 template <int kOut>
 __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in, void* __restrict__ out,
                              const float* __restrict__ scales, uint64_t g, DecShared& sm, LaneDec& d,
-                             uint32_t* status, int lane, bool aligned32) {
+                             uint32_t* status, int lane, bool aligned32, bool sc_vec = false) {
   const unsigned long long* group_off = reinterpret_cast<const unsigned long long*>(in + kIndexOff);
   const uint16_t* chunk_bits = reinterpret_cast<const uint16_t*>(in + kIndexOff + 8 * h.n_groups);
   const uint4* vbase = reinterpret_cast<const uint4*>(in + h.P);
@@ -432,8 +398,31 @@ __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* 
   d.start(sm, S);
   const uint64_t i_chunk = c * cs;  // the chunk's first symbol
   const uint32_t nmax = __reduce_max_sync(0xffffffffu, nsym);
+  // dequantising outputs: the scales of the chunk's whole blocks, four per
+  // 16-byte load (a lane's loads hit lines of their own, so four scales per
+  // load cut the load traffic of the L1 data pipe fourfold), each four
+  // loaded four blocks before their use
+  const uint32_t nfull = nsym / kBlk;
+  const float* sc_chunk = kOut != kOutCodes ? scales + i_chunk / 32 : nullptr;
+  auto scales4 = [&](uint32_t q) {  // scales of whole blocks 4q .. 4q + 3 (0 past the last)
+    float4 r = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (kOut == kOutCodes) return r;
+    if (4 * q + 4 <= nfull && sc_vec) return __ldg(reinterpret_cast<const float4*>(sc_chunk + 4 * q));
+    if (4 * q < nfull) r.x = sc_chunk[4 * q];
+    if (4 * q + 1 < nfull) r.y = sc_chunk[4 * q + 1];
+    if (4 * q + 2 < nfull) r.z = sc_chunk[4 * q + 2];
+    if (4 * q + 3 < nfull) r.w = sc_chunk[4 * q + 3];
+    return r;
+  };
+  float4 sc_cur = make_float4(0.0f, 0.0f, 0.0f, 0.0f), sc_nxt = scales4(0);
   for (uint32_t i0 = 0; i0 < nmax; i0 += kBlk) {
     d.advance();
+    const uint32_t b = i0 / kBlk;  // the same block index in every lane
+    if (kOut != kOutCodes && (b & 3u) == 0) {
+      sc_cur = sc_nxt;
+      sc_nxt = scales4(b / 4 + 1);
+    }
+    const float sc = (b & 3u) == 0 ? sc_cur.x : (b & 3u) == 1 ? sc_cur.y : (b & 3u) == 2 ? sc_cur.z : sc_cur.w;
     const uint32_t cnt = nsym > i0 ? min(kBlk, nsym - i0) : 0u;
     if (cnt == kBlk) {
       uint32_t w[8];
@@ -443,7 +432,7 @@ __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* 
         const uint32_t p1 = d.round2(sm, len_lo, len_hi);
         w[j] = __byte_perm(p0, p1, 0x5410);
       }
-      if (QLC_GUARD(i_chunk + i0 + kBlk <= h.out_cap, status)) put32<kOut>(out, scales, i_chunk + i0, w, aligned32);
+      if (QLC_GUARD(i_chunk + i0 + kBlk <= h.out_cap, status)) put32<kOut>(out, sc, i_chunk + i0, w, aligned32);
     } else {
       for (uint32_t k = 0; k < cnt; k++) {
         const uint32_t sym = d.round1(sm, len_lo, len_hi);
@@ -491,8 +480,9 @@ decode_kernel(const uint8_t* __restrict__ in, uint64_t in_bytes, void* __restric
   }
   build_table(in, sm, lane);
   const bool aligned32 = (reinterpret_cast<uintptr_t>(out) & 31u) == 0;
+  const bool sc_vec = (reinterpret_cast<uintptr_t>(scales) & 15u) == 0;  // scales read four at a time
   for (uint64_t g = blockIdx.x; g < h.n_groups; g += gridDim.x)
-    decode_group<kOut>(h, in, out, scales, g, sm, d, status, lane, aligned32);
+    decode_group<kOut>(h, in, out, scales, g, sm, d, status, lane, aligned32, sc_vec);
 }
 
 // A batch: warps take (shard, group) items from a device counter; a warp

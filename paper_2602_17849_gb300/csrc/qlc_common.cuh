@@ -134,6 +134,13 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
 __device__ __forceinline__ float e4m3_to_f32(uint32_t c) {
   return __uint_as_float(((c & 0x80u) << 24) | ((c & 0x7Fu) << 20)) * 0x1p120f;
 }
+// The same bit pattern (value 2^-120 times) for byte j of w: the byte moved
+// to the top (sign at bit 31), an arithmetic shift right by 4 (the
+// magnitude to bits 26..20, the sign repeated above it), bits 30..27 cleared.
+__device__ __forceinline__ uint32_t e4m3_scaled_bits(uint32_t w, int j) {
+  const uint32_t t = __byte_perm(w, 0u, 0x0444u | ((uint32_t)j << 12));
+  return (uint32_t)((int32_t)t >> 4) & 0x87F00000u;
+}
 
 // The shard holding work item t of a batch: the largest s < n_shards with
 // item_base[s] <= t (item_base is non-decreasing and item_base[0] = 0, so

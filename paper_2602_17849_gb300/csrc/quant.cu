@@ -324,7 +324,7 @@ dequantize_kernel(const uint8_t* __restrict__ codes, const float* __restrict__ s
     }
     float y[16];
 #pragma unroll
-    for (int j = 0; j < 16; j++) y[j] = e4m3_to_f32((w[j >> 2] >> (8 * (j & 3))) & 0xFFu) * sc;
+    for (int j = 0; j < 16; j++) y[j] = __uint_as_float(e4m3_scaled_bits(w[j >> 2], j & 3)) * 0x1p120f * sc;
     if (kDtype == QLC_DTYPE_F32) {
       float* o = static_cast<float*>(out) + i;
       if (i + 16 <= n) {
