@@ -303,54 +303,51 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
   }
 }
 
-// out[i] = value(codes[i]) * scales[i / 32]; 16 codes per lane per step.
+// out[i] = value(codes[i]) * scales[i / 32].  Warp step s covers codes
+// [512 s, 512 s + 512); in part k (0..3) lane l takes codes
+// [512 s + 128 k + 4 l, + 4), so each load and store instruction of the warp
+// covers contiguous bytes (128 bytes of codes, 512 of fp32 or 256 of bf16).
 template <int kDtype>
 __global__ void __launch_bounds__(256)
 dequantize_kernel(const uint8_t* __restrict__ codes, const float* __restrict__ scales, uint64_t n,
                   void* __restrict__ out) {
-  const uint64_t n16 = (n + 15) / 16;
-  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n16; t += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t i = t * 16;
-    const float sc = scales[i / 32];
-    uint32_t w[4];
-    if (i + 16 <= n) {
-      const uint4 q = ldg_nc_v4(reinterpret_cast<const uint4*>(codes + i));
-      w[0] = q.x, w[1] = q.y, w[2] = q.z, w[3] = q.w;
-    } else {
-      w[0] = w[1] = w[2] = w[3] = 0;
+  const int lane = threadIdx.x & 31;
+  const uint64_t n_steps = (n + 511) / 512;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x / 32);
+  for (uint64_t s = (uint64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; s < n_steps; s += warps) {
 #pragma unroll
-      for (int j = 0; j < 16; j++)
-        if (i + j < n) w[j >> 2] |= (uint32_t)codes[i + j] << (8 * (j & 3));
-    }
-    float y[16];
-#pragma unroll
-    for (int j = 0; j < 16; j++) y[j] = __uint_as_float(e4m3_scaled_bits(w[j >> 2], j & 3)) * 0x1p120f * sc;
-    if (kDtype == QLC_DTYPE_F32) {
-      float* o = static_cast<float*>(out) + i;
-      if (i + 16 <= n) {
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-          __stcs(reinterpret_cast<float4*>(o) + k, make_float4(y[4 * k], y[4 * k + 1], y[4 * k + 2], y[4 * k + 3]));
+    for (int k = 0; k < 4; k++) {
+      const uint64_t i = s * 512 + 128 * k + 4 * lane;
+      if (i >= n) continue;
+      const float sc = scales[i / 32];
+      uint32_t w = 0;
+      if (i + 4 <= n) {
+        w = __ldg(reinterpret_cast<const unsigned int*>(codes + i));
       } else {
-#pragma unroll
-        for (int j = 0; j < 16; j++)
-          if (i + j < n) o[j] = y[j];
+        for (int j = 0; j < 4; j++)
+          if (i + j < n) w |= (uint32_t)codes[i + j] << (8 * j);
       }
-    } else {
-      __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + i;
-      if (i + 16 <= n) {
-        uint32_t p[8];
+      float y[4];
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-          const __nv_bfloat162 h = __floats2bfloat162_rn(y[2 * k], y[2 * k + 1]);
-          p[k] = *reinterpret_cast<const uint32_t*>(&h);
+      for (int j = 0; j < 4; j++) y[j] = __uint_as_float(e4m3_scaled_bits(w, j)) * 0x1p120f * sc;
+      if (kDtype == QLC_DTYPE_F32) {
+        float* o = static_cast<float*>(out) + i;
+        if (i + 4 <= n) {
+          __stcs(reinterpret_cast<float4*>(o), make_float4(y[0], y[1], y[2], y[3]));
+        } else {
+          for (int j = 0; j < 4; j++)
+            if (i + j < n) o[j] = y[j];
         }
-        __stcs(reinterpret_cast<uint4*>(o), make_uint4(p[0], p[1], p[2], p[3]));
-        __stcs(reinterpret_cast<uint4*>(o) + 1, make_uint4(p[4], p[5], p[6], p[7]));
       } else {
-#pragma unroll
-        for (int j = 0; j < 16; j++)
-          if (i + j < n) o[j] = __float2bfloat16_rn(y[j]);
+        __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out) + i;
+        if (i + 4 <= n) {
+          const __nv_bfloat162 h0 = __floats2bfloat162_rn(y[0], y[1]), h1 = __floats2bfloat162_rn(y[2], y[3]);
+          __stcs(reinterpret_cast<uint2*>(o), make_uint2(*reinterpret_cast<const uint32_t*>(&h0),
+                                                         *reinterpret_cast<const uint32_t*>(&h1)));
+        } else {
+          for (int j = 0; j < 4; j++)
+            if (i + j < n) o[j] = __float2bfloat16_rn(y[j]);
+        }
       }
     }
   }
@@ -425,7 +422,7 @@ extern "C" qlc_status qlc_dequantize_e4m3(const uint8_t* d_codes, const float* d
   if (n > 0 && (!d_codes || !d_scales || !d_out)) return QLC_ERR_ARG;
   if (!aligned(d_codes, 16) || !aligned(d_out, 16) || !aligned(d_scales, 4)) return QLC_ERR_ARG;
   if (n == 0) return QLC_OK;
-  const uint64_t want = ((n + 15) / 16 + 255) / 256;
+  const uint64_t want = ((n + 511) / 512 + 7) / 8;  // warp steps of 512 codes, 8 warps per CTA
   const uint64_t cap = (uint64_t)sm_count() * 8;
   const int grid = (int)(want < cap ? want : cap);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -62,7 +62,10 @@ def _as_f32_host(x: torch.Tensor) -> np.ndarray:
     return x.numpy()
 
 
-@pytest.mark.parametrize("n", [1, 31, 32, 33, 127, 128, 129, 255, 257, 1000, 32 * 4096 + 17, 1 << 20])
+# (1 << 23) + 37: every warp of the resident grid takes several steps through its
+# input ring, and the ragged last step follows full ones
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 127, 128, 129, 255, 257, 1000, 32 * 4096 + 17, 1 << 20,
+                               (1 << 23) + 37])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_quantize_matches_oracle(qlc, n, dtype):
     x = _floats(n, seed=n).to(dtype)
