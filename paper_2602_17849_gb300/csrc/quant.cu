@@ -10,9 +10,10 @@
 // kept; a block whose scale is 0 (absmax 0, or absmax / 480 rounding to 0 in
 // fp32) gets codes 0x00.
 //
-// A warp handles 32 x 16 bytes of input per step: 4 fp32 (or 8 bf16) elements
-// per lane, so one block of 32 is 8 (or 4) lanes and its absmax is a 3 (or 2)
-// step butterfly.  Codes leave as one 4- (or 8-) byte store per lane.
+// A warp handles 1 KiB of input per step: 32 contiguous bytes per lane, 8
+// fp32 (or 16 bf16) elements, so one block of 32 is 4 (or 2) lanes and its
+// absmax is a 2 (or 1) step butterfly.  Codes leave as one 8- (or 16-) byte
+// store per lane.
 #include <cuda_bf16.h>
 
 #include <atomic>
@@ -24,7 +25,7 @@ namespace qlc {
 
 constexpr int kQuantWarps = 8;
 constexpr int kQuantThreads = kQuantWarps * 32;
-constexpr int kQuantDepth = 4;  // input ring slots per thread
+constexpr int kQuantDepth = 4;  // input ring slots (warp steps) per warp
 constexpr int kQuantVec = 2;    // 16-byte input vectors per lane and step
 
 // The e4m3 byte nearest to v, ties to the even code, saturating (|v| finite).
