@@ -86,13 +86,17 @@ def test_quantize_non_finite_is_an_argument_error(qlc):
         assert st == ost == oracle.ERR_ARG
 
 
-@pytest.mark.parametrize("n", [1, 17, 32, 1000, 32 * 4096 + 17])
+# (1 << 24) + 9: several 512-code warp steps per warp and a ragged last step
+@pytest.mark.parametrize("n", [1, 17, 32, 1000, 32 * 4096 + 17, (1 << 24) + 9])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_dequantize_matches_oracle(qlc, n, dtype):
     rng = np.random.default_rng(n)
     codes = rng.integers(0, 256, n, dtype=np.uint8)
     scales = (rng.standard_normal((n + 31) // 32) ** 2 * 0.01).astype(np.float32)
     scales[0] = 0.0
+    if scales.size > 3:
+        scales[1] = 3.0e35   # values near the fp32 maximum
+        scales[2] = 1e-40    # a subnormal scale: subnormal products
     out = torch.empty(max(n, 16), dtype=dtype, device="cuda")
     qlc.qlc_dequantize_e4m3(torch.from_numpy(codes).cuda(), torch.from_numpy(scales).cuda(), out, n=n)
     torch.cuda.synchronize()
