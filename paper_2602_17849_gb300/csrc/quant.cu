@@ -73,6 +73,21 @@ __device__ __forceinline__ void e4m3x2_bracket(float qa, float qb, uint32_t* up,
   *lo = (uint32_t)cl | (sat_flags(la, lb) & 0x0101u);
 }
 
+// amax / 480 rounded to nearest.  For amax in [2^-100, FLT_MAX] a product
+// with 1/480 (rounded) and one correction by its fused-multiply-add residual
+// (Markstein's correction step) give the correctly rounded quotient; checked
+// against the division for every float with an exponent in that range (the
+// quotient's pattern repeats from binade to binade there).  Other values
+// (zero, tiny, non-finite) take the division.
+__device__ __forceinline__ float scale_of(float amax) {
+  constexpr float c = 1.0f / 480.0f;
+  if (amax >= 0x1p-100f && amax <= 3.40282347e38f) {
+    const float q0 = amax * c;
+    return fmaf(fmaf(-q0, 480.0f, amax), c, q0);
+  }
+  return amax / 480.0f;
+}
+
 // max(a, b) that returns NaN when either is NaN.
 __device__ __forceinline__ float fmax_nan(float a, float b) {
   float r;
@@ -142,7 +157,7 @@ __device__ __forceinline__ float lane_codes(const float (&v)[E], uint32_t (&w)[E
   bad |= !(amax <= 3.402823466e38f);  // NaN or infinity in this lane
 #pragma unroll
   for (int o = 1; o < kLanesPerBlock; o <<= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  const float scale = amax / 480.0f;
+  const float scale = scale_of(amax);
   // one reciprocal per lane and block, within 2 ulp for scale in
   // [2^-126, 2^126]; a scale below 2^-125 takes the exact division for
   // every element

@@ -234,3 +234,34 @@ def test_quantize_near_midpoints(qlc, lo, hi):
     assert np.array_equal(scales.view(np.uint32), oscales.view(np.uint32))
     assert np.array_equal(codes, ocodes)
     assert np.array_equal(hist, oracle.histogram(ocodes))
+
+
+def test_scale_for_every_mantissa(qlc):
+    """Block scales against numpy's float32 division for every mantissa of
+    amax in [1, 2), and for amax in the binades where the kernel switches
+    between its corrected product and the division (2^-101, 2^-100) and at
+    the top of the float range."""
+    m = 1 << 23
+    a = (np.arange(m, dtype=np.uint32) | np.uint32(0x3F800000)).view(np.float32)
+    rng = np.random.default_rng(5)
+    edge = np.concatenate([
+        (rng.integers(0, m, 4096, dtype=np.uint32) | np.uint32(26 << 23)).view(np.float32),   # 2^-101
+        (rng.integers(0, m, 4096, dtype=np.uint32) | np.uint32(27 << 23)).view(np.float32),   # 2^-100
+        (rng.integers(0, m, 4096, dtype=np.uint32) | np.uint32(254 << 23)).view(np.float32),  # 2^127
+        np.array([np.float32(2.0 ** -100), np.nextafter(np.float32(2.0 ** -100), np.float32(0)),
+                  np.finfo(np.float32).max, np.float32(1e-45)], dtype=np.float32)])
+    amax = np.concatenate([a, edge])
+    x = torch.zeros(amax.size, 32, dtype=torch.float32, device="cuda")
+    am = torch.from_numpy(amax).cuda()
+    x[:, 0] = am
+    x[:, 7] = -am * 0.25
+    x = x.reshape(-1)
+    n = x.numel()
+    codes = torch.empty(n, dtype=torch.uint8, device="cuda")
+    scales = torch.empty(n // 32, dtype=torch.float32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    qlc.qlc_quantize_e4m3(x, codes, scales, None, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    want = amax / np.float32(480.0)
+    assert np.array_equal(scales.cpu().numpy().view(np.uint32), want.view(np.uint32))
