@@ -215,10 +215,10 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
   constexpr uint32_t kStep = 32 * E;             // elements per warp step
   constexpr uint32_t kWords = E / 4;             // code words per lane
   constexpr uint32_t kSlot = kQuantWarps * kQuantVec * 512u;  // bytes of a ring slot
-  __shared__ uint32_t sh[kQuantWarps][257];
+  __shared__ uint32_t sh[kQuantWarps][256];  // per-warp histograms
   __shared__ uint4 ring[kQuantDepth][kQuantWarps][kQuantVec * 32];
   if (hist) {
-    for (int i = threadIdx.x; i < kQuantWarps * 257; i += kQuantThreads) (&sh[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kQuantWarps * 256; i += kQuantThreads) (&sh[0][0])[i] = 0;
     __syncthreads();
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -259,7 +259,7 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
     for (int j = 0; j < E; j++) {
       if (j < m) {
         const uint32_t c = __byte_perm(w[j / 4], 0, 0x4440 + (j % 4));
-        atomicAdd(&my[c + (c >> 7)], 1u);
+        atomicAdd(&my[c], 1u);
       }
     }
   };
@@ -313,7 +313,7 @@ quantize_kernel(const void* __restrict__ x, uint64_t n, uint8_t* __restrict__ co
     for (int b = threadIdx.x; b < 256; b += kQuantThreads) {
       uint32_t t = 0;
 #pragma unroll
-      for (int w = 0; w < kQuantWarps; w++) t += sh[w][b + (b >> 7)];
+      for (int w = 0; w < kQuantWarps; w++) t += sh[w][b];
       if (t) atomicAdd(&hist[b], (unsigned long long)t);
     }
   }
