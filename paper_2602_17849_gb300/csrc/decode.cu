@@ -535,10 +535,24 @@ decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
 
 using namespace qlc;
 
+// One CTA (warp) per group where the container's groups are few enough, up
+// to kDecCtasPerSm per SM.  The host knows out_cap, not the chunk size: a
+// container of out_cap symbols has between min_groups (chunks of
+// QLC_MAX_CHUNK) and max_groups (chunks of QLC_MIN_CHUNK) groups.  A grid
+// much larger than the groups lets the block scheduler put up to 16 of the
+// working CTAs on some SMs and 13 on others (measured with 2048 groups: a
+// grid of 2048 or 2128 CTAs gives every SM 13 or 14 working CTAs, grids of
+// 2432 or 3040 up to 16, and decode runs 4 % slower).  So a container large
+// enough to fill the GPU at the largest chunk gets min_groups CTAs: every CTA
+// works at that chunk, and at smaller chunks each CTA takes several groups.
 static int decode_grid(uint64_t out_cap) {
-  const uint64_t max_groups = (out_cap + kGroupChunks * QLC_MIN_CHUNK - 1) / (kGroupChunks * QLC_MIN_CHUNK);
-  const uint64_t cap = (uint64_t)sm_count() * kDecCtasPerSm;
-  return (int)(max_groups < 1 ? 1 : (max_groups < cap ? max_groups : cap));
+  const uint64_t per_group_min = (uint64_t)kGroupChunks * QLC_MIN_CHUNK;
+  const uint64_t per_group_max = (uint64_t)kGroupChunks * QLC_MAX_CHUNK;
+  const uint64_t max_groups = (out_cap + per_group_min - 1) / per_group_min;
+  const uint64_t min_groups = (out_cap + per_group_max - 1) / per_group_max;
+  const uint64_t sms = (uint64_t)sm_count(), cap = sms * kDecCtasPerSm;
+  const uint64_t want = min_groups >= 2 * sms ? min_groups : max_groups;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
 extern "C" qlc_status qlc_decode(const uint8_t* d_in, size_t in_bytes, uint8_t* d_out, size_t out_cap,
