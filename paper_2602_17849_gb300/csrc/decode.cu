@@ -358,11 +358,16 @@ __device__ __forceinline__ void put1(void* out, const float* scales, uint64_t i,
   put_tail<kOut>(out, scales, i, &b, 1);
 }
 
-// Decodes group g of a validated container (one warp; lane = chunk).
+// Decodes group g of a validated container (one warp; lane = chunk).  With
+// out_slot the output pointer is read from that shared word at each block
+// instead of out: a pointer that is not a kernel parameter would otherwise
+// hold two registers across the decoding loop, which then issued about 10 %
+// more instructions (the batch decoder, 124.3 M against 112.8 M on 256 MiB).
 template <int kOut>
 __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* __restrict__ in, void* __restrict__ out,
                              const float* __restrict__ scales, uint64_t g, DecShared& sm, LaneDec& d,
-                             uint32_t* status, int lane, bool aligned32, bool sc_vec = false) {
+                             uint32_t* status, int lane, bool aligned32, bool sc_vec = false,
+                             void* const volatile* out_slot = nullptr) {
   const unsigned long long* group_off = reinterpret_cast<const unsigned long long*>(in + kIndexOff);
   const uint16_t* chunk_bits = reinterpret_cast<const uint16_t*>(in + kIndexOff + 8 * h.n_groups);
   const uint4* vbase = reinterpret_cast<const uint4*>(in + h.P);
@@ -424,6 +429,7 @@ __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* 
     }
     const float sc = (b & 3u) == 0 ? sc_cur.x : (b & 3u) == 1 ? sc_cur.y : (b & 3u) == 2 ? sc_cur.z : sc_cur.w;
     const uint32_t cnt = nsym > i0 ? min(kBlk, nsym - i0) : 0u;
+    void* o = out_slot ? *out_slot : out;
     if (cnt == kBlk) {
       uint32_t w[8];
 #pragma unroll
@@ -432,11 +438,11 @@ __device__ __forceinline__ void decode_group(const DecHeader& h, const uint8_t* 
         const uint32_t p1 = d.round2(sm, len_lo, len_hi);
         w[j] = __byte_perm(p0, p1, 0x5410);
       }
-      if (QLC_GUARD(i_chunk + i0 + kBlk <= h.out_cap, status)) put32<kOut>(out, sc, i_chunk + i0, w, aligned32);
+      if (QLC_GUARD(i_chunk + i0 + kBlk <= h.out_cap, status)) put32<kOut>(o, sc, i_chunk + i0, w, aligned32);
     } else {
       for (uint32_t k = 0; k < cnt; k++) {
         const uint32_t sym = d.round1(sm, len_lo, len_hi);
-        if (QLC_GUARD(i_chunk + i0 + k < h.out_cap, status)) put1<kOut>(out, scales, i_chunk + i0 + k, sym);
+        if (QLC_GUARD(i_chunk + i0 + k < h.out_cap, status)) put1<kOut>(o, scales, i_chunk + i0 + k, sym);
       }
     }
   }
@@ -501,6 +507,7 @@ decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
   const unsigned long long total = item_base[n_shards];
   int cur = -1, bad = -1;
   DecHeader h;
+  __shared__ void* volatile s_out;  // the current item's output
   while (true) {
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(ticket, 1u);
@@ -527,7 +534,11 @@ decode_batch_kernel(const qlc_desc* __restrict__ descs, int n_shards,
     }
     if (g == 0 && lane == 0 && dd.out_bytes) *dd.out_bytes = h.n;
     const bool aligned32 = (reinterpret_cast<uintptr_t>(dd.out) & 31u) == 0;
-    if (g < h.n_groups) decode_group<kOutCodes>(h, in, dd.out, nullptr, g, sm, d, status, lane, aligned32);
+    __syncwarp();  // every lane is done with the previous item's output
+    if (lane == 0) s_out = dd.out;
+    __syncwarp();
+    if (g < h.n_groups)
+      decode_group<kOutCodes>(h, in, nullptr, nullptr, g, sm, d, status, lane, aligned32, false, &s_out);
   }
 }
 
