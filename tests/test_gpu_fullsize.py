@@ -46,3 +46,33 @@ def test_full_size_256mib_matches_oracle():
     h = oracle.histogram(xh)
     code_only = 1 - oracle.code_bits(h, oracle.scheme(1)) / (8 * N)
     assert abs(code_only - (1 - got.size / N)) < 0.001
+
+
+@pytest.mark.parametrize("cs", [128, 1024])
+def test_large_container_small_chunks_and_spare_output(cs):
+    """64 MiB with small chunks: the single-tensor decoder sizes its grid by
+    the group count at the largest chunk (512 CTAs here), so each CTA decodes
+    8 (chunk 1024) or 64 (chunk 128) groups in turn.  Decoding into an output
+    twice the size puts more CTAs than groups on the grid.  Both give the
+    input back, from a container equal to the oracle's."""
+    from paper_2602_17849_gb300 import _build
+    _build.build()
+    from paper_2602_17849_gb300 import qlc
+    n = 64 << 20
+    x = inputs.make_e4m3("t4", n, seed=4, device="cuda")
+    codec = qlc.Codec(n, cs, 1, "cuda")
+    cont = codec.new_container()
+    codec.encode_into(x, cont)
+    torch.cuda.synchronize()
+    codec.check()
+    nbytes = int(codec.out_bytes.item())
+    want = oracle.encode(x.cpu().numpy(), scheme_id=1, chunk_symbols=cs)
+    assert np.array_equal(cont[:nbytes].cpu().numpy(), want)
+    for out_n in (n, 2 * n):
+        y = torch.full((out_n,), 0xAB, dtype=torch.uint8, device="cuda")
+        qlc.qlc_decode(cont, y, codec.n_out, codec.status, in_bytes=nbytes, out_cap=out_n)
+        torch.cuda.synchronize()
+        codec.check()
+        assert int(codec.n_out.item()) == n
+        assert torch.equal(y[:n], x)
+        assert bool((y[n:] == 0xAB).all())
