@@ -225,7 +225,7 @@ typedef struct qlc_desc {
 /* Launch shape knobs (an autotuner picks them); 0 = library default. */
 typedef struct qlc_launch {
   uint16_t encode_ctas_per_sm; /* resident encode CTAs (256 threads) per SM, 1..3 */
-  uint16_t decode_ctas_per_sm; /* resident decode warps per SM, 1..26 */
+  uint16_t decode_ctas_per_sm; /* resident decode warps per SM, 1..20 (larger: 20) */
   uint32_t reserved;
 } qlc_launch;
 
