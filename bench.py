@@ -563,9 +563,16 @@ def fused_leg(dev, steps: int, warmup: int, peak: float, n: int = N_BYTES):
     codec.check()
     c_bytes = int(codec.out_bytes.item())
     assert torch.equal(y.view(torch.int32), y2.view(torch.int32)) and torch.equal(codes, codes2)
-    # quantise + histogram alone, for its roofline
+    # quantise + histogram alone, for its roofline; dequantise alone; bf16 input
     t_q = timed(lambda: qlc.qlc_quantize_e4m3(x, codes, scales, codec.hist, codec.status, stream=stream))
+    t_dq = timed(lambda: qlc.qlc_dequantize_e4m3(codes2, scales, y2, stream=stream))
+    xb = x.to(torch.bfloat16)
+    t_qb = timed(lambda: qlc.qlc_quantize_e4m3(xb, codes2, scales, codec.hist, codec.status, stream=stream))
+    codec.check()
+    del xb
     q_bytes = 4 * n + n + n // 8
+    qb_bytes = 2 * n + n + n // 8
+    dq_bytes = n + n // 8 + 4 * n
     d_bytes = c_bytes + n // 8 + 4 * n
     return {
         "workload": f"{n} fp32 Student-t(4) activations, block-32 e4m3, chunk 4096, Table 1",
@@ -573,8 +580,11 @@ def fused_leg(dev, steps: int, warmup: int, peak: float, n: int = N_BYTES):
         "encode_fused_gbs_fp32": 4 * n / (t_ef * 1e-3) / 1e9, "decode_fused_gbs_fp32": 4 * n / (t_df * 1e-3) / 1e9,
         "speedup_encode": t_ep / t_ef, "speedup_decode": t_dp / t_df,
         "quantize_hist_ms": t_q, "quantize_hist_roofline_frac": q_bytes / (t_q * 1e-3) / 1e9 / peak,
+        "quantize_hist_bf16_ms": t_qb, "quantize_hist_bf16_roofline_frac": qb_bytes / (t_qb * 1e-3) / 1e9 / peak,
+        "dequantize_ms": t_dq, "dequantize_roofline_frac": dq_bytes / (t_dq * 1e-3) / 1e9 / peak,
         "decode_dequantize_roofline_frac": d_bytes / (t_df * 1e-3) / 1e9 / peak,
-        "bytes_counted": "quantise+hist: 4N read + N codes + N/8 scales written; decode->fp32: C + N/8 read, 4N written",
+        "bytes_counted": "quantise+hist: 4N (bf16: 2N) read + N codes + N/8 scales written; dequantise: N + N/8 "
+                         "read, 4N written; decode->fp32: C + N/8 read, 4N written",
         "bit_exact_vs_unfused": True,
     }
 
