@@ -118,6 +118,53 @@ def main():
     assert ost == 0 and np.array_equal(codes.cpu().numpy(), ocodes)
     want = oracle.dequantize_block32(ocodes, oscales)
     assert np.array_equal(yf.cpu().numpy().view(np.uint32), want.view(np.uint32))
+    # larger sizes: every quantiser warp steps through its input ring several
+    # times before a ragged last step, and the decoder's grid is one CTA per
+    # group with the block scales read four at a time
+    rng2 = np.random.default_rng(23)
+    n = (1 << 23) + 37
+    for dt in (torch.float32, torch.bfloat16):
+        xq = inputs.make_f32("t4", n, seed=5, device="cuda").to(dt)
+        codes = torch.empty(n, dtype=torch.uint8, device="cuda")
+        scales = torch.empty((n + 31) // 32, dtype=torch.float32, device="cuda")
+        hist = torch.zeros(256, dtype=torch.int64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        qlc.qlc_quantize_e4m3(xq, codes, scales, hist, st)
+        torch.cuda.synchronize()
+        clean(f"quantise {dt} n={n}")
+        assert int(st.item()) == 0
+        assert torch.equal(hist, torch.bincount(codes.long(), minlength=256))
+        blocks = np.append(rng2.choice(n // 32, 256, replace=False), n // 32)  # and the ragged last block
+        xh = xq.cpu()
+        xh = (oracle.bf16_to_f32(xh.view(torch.int16).numpy().view(np.uint16)) if dt == torch.bfloat16
+              else xh.numpy())
+        ch, sh = codes.cpu().numpy(), scales.cpu().numpy()
+        for blk in blocks:
+            lo, hi = 32 * int(blk), min(32 * int(blk) + 32, n)
+            ost, oc, osc = oracle.quantize_block32(xh[lo:hi])
+            assert ost == 0 and np.array_equal(ch[lo:hi], oc) and sh[blk].view(np.uint32) == osc[0].view(np.uint32)
+    n = 48 << 20
+    xf = inputs.make_f32("t4", n, seed=6, device="cuda")
+    codes = torch.empty(n, dtype=torch.uint8, device="cuda")
+    scales = torch.empty(n // 32, dtype=torch.float32, device="cuda")
+    fc = qlc.Codec(n, 4096, 1)
+    qlc.qlc_quantize_e4m3(xf, codes, scales, fc.hist, fc.status)
+    qlc.qlc_build_lut(fc.hist, 1, fc.lut)
+    fcont = fc.new_container()
+    fc.encode_into(codes, fcont, build_lut=False)
+    torch.cuda.synchronize()
+    fb = int(fc.out_bytes.item())
+    yf = torch.empty(n, dtype=torch.float32, device="cuda")
+    qlc.qlc_decode_dequantize(fcont, scales, yf, fc.n_out, fc.status, in_bytes=fb)
+    ref = torch.empty(n, dtype=torch.float32, device="cuda")
+    qlc.qlc_dequantize_e4m3(codes, scales, ref)
+    yc = torch.empty(n, dtype=torch.uint8, device="cuda")
+    qlc.qlc_decode(fcont, yc, fc.n_out, fc.status, in_bytes=fb)
+    torch.cuda.synchronize()
+    fc.check()
+    clean(f"quantise, encode, decode and decode to fp32, n={n}")
+    assert torch.equal(yc, codes)
+    assert torch.equal(yf.view(torch.int32), ref.view(torch.int32))
     print(f"checked build: {cases} cases, no index check failed")
 
 
